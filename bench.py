@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: batched FWI gradient (32 shots, 512 x 256 at 6.25 m, nt = 4000)
+on one GB300 per rank, through libwave's C ABI.
+
+A step is one full gradient evaluation of the 32-shot batch: forward sweep
+(source injection, receiver gather), misfit, adjoint sweep with the fused
+zero-lag imaging condition, binomial-checkpoint recomputation, and the shot
+sum.  ``value`` is shot-gradients per second over all ranks; grid-point
+updates per second, the plain one-shot-at-a-time rate, the BF16-store rate,
+an end-to-end rate through host buffers, the roofline of the dominant stencil
+kernel and the FP64 oracle on the host cores are reported beside it.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt updates/s & shot-gradients/s (batched vs plain, ≤1e-3 rel L2); HBM roofline %"
+UNIT = "shot-gradients/s"
+WORKLOAD = ("2D FWI gradient, 32 shots: 512x256 at 6.25 m, layered 1500-3500 m/s + 5% Gaussian-random "
+            "perturbation (100 m), 512 receivers, 20 Hz Ricker, nt=4000 at dt=0.5 ms, 40-cell sponge, FP32, "
+            "binomial checkpointing")
+FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# the SHA-256 of the kernel source they were taken on; dropped (null) once the source changes.
+TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nsnap", type=int, default=256, help="checkpoint slots (two FP32 fields per shot each)")
+    ap.add_argument("--nshot", type=int, default=32)
+    ap.add_argument("--nt", type=int, default=4000)
+    ap.add_argument("--only-main", action="store_true", help="timed gradient steps only (for launch lists)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def kernel_hash() -> str:
+    with open(os.path.join(ROOT, "paper_2304_05592_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_problem(nshot: int, nt: int):
+    from paper_2304_05592_gb300 import synth
+
+    p = synth.config2(nshot=32, nt=nt)
+    if nshot != 32:
+        p = p.with_shots(np.arange(nshot) % 32)
+    from scipy.ndimage import gaussian_filter
+
+    v0 = gaussian_filter(p.vel.astype(np.float64), 8.0).astype(np.float32)  # smooth starting model
+    return p, v0
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores.
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    p, v0 = make_problem(1, args.nt)
+    g = oracle.Grid(2, p.nx, p.nz, p.h, p.dt, p.nt, p.nb, vref=p.vref)
+    q = oracle.ricker(p.f0, p.dt, p.nt)[None, :, None]
+    dobs = oracle.forward(g, p.vel, p.src, q, p.rec)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        oracle.gradient(g, v0, p.src, q, p.rec, dobs)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = args.steps / tot
+    sample = f"1 of the 32 shots per step (full nt={p.nt}, full grid), FP64, OpenMP over grid rows"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nshot_per_step": 1, "nt": p.nt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm.
+
+
+def cpu_baseline(nt: int):
+    import oracle
+
+    oracle.build()
+    p, v0 = make_problem(1, nt)
+    g = oracle.Grid(2, p.nx, p.nz, p.h, p.dt, p.nt, p.nb, vref=p.vref)
+    q = oracle.ricker(p.f0, p.dt, p.nt)[None, :, None]
+    dobs = oracle.forward(g, p.vel, p.src, q, p.rec)
+    t = time.perf_counter()
+    oracle.gradient(g, v0, p.src, q, p.rec, dobs)
+    el = time.perf_counter() - t
+    return {"value": 1.0 / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"1 shot of the 32 (full grid, nt={nt}), one gradient, FP64, {el:.1f} s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2304_05592_gb300 import wave
+    from paper_2304_05592_gb300.wave import Grid
+
+    p, v0 = make_problem(args.nshot, args.nt)
+    grid = Grid.of(p)
+    vel_true = torch.from_numpy(p.vel).to(dev)
+    vel = torch.from_numpy(v0).to(dev)
+    q1 = wave.wave_ricker(p.f0, p.dt, p.nt, device=dev)
+    wavelet = q1[None, :, None].repeat(p.nshot, 1, 1).contiguous()
+    d_obs = wave.wave_forward(grid, vel_true, p.src, wavelet, p.rec)
+    store = wave.STORE_CHECKPOINT
+    nbytes = wave.wave_workspace_size(grid, wave.OP_GRADIENT, p.src, p.rec, store, args.nsnap)
+    work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    grad = torch.empty(grid.phys_shape, dtype=torch.float32, device=dev)
+
+    def step():
+        phi, g, _ = wave.wave_gradient(grid, vel, p.src, wavelet, p.rec, d_obs, store=store, nsnap=args.nsnap,
+                                       grad=grad, work=work)
+        if world > 1:
+            dist.all_reduce(g)  # shot-summed gradient across ranks
+        return phi
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = wave.wave_launch_count()
+    wave.wave_profile_start(8)
+    barrier()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    fwd_ms, fwd_n, adj_ms, adj_n = wave.wave_profile_stop()
+    launches = wave.wave_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    sec = ms / 1e3
+    value = p.nshot * args.steps * world / sec
+    N = p.padded_points
+    updates = 2.0 * (p.nt - 1) * N * p.nshot * args.steps * world  # forward + adjoint steps (recompute excluded)
+    sched_steps, _ = wave.wave_checkpoint_schedule(p.nt, args.nsnap)
+
+    # roofline of the dominant stencil kernel (event-timed samples of the timed region)
+    peak, peak_kind = hbm_peak()
+    f_avg = fwd_ms / max(fwd_n, 1) / 1e3
+    a_avg = adj_ms / max(adj_n, 1) / 1e3
+    n_fwd_launch = sched_steps * args.steps
+    n_adj_launch = (p.nt - 1) * args.steps
+    pts = N * p.nshot
+    kern = {"fwd": {"name": "k_step2d<32,8,false>", "bytes": 16 * pts, "avg_s": f_avg,
+                    "total_s": f_avg * n_fwd_launch, "launches": n_fwd_launch},
+            "adj": {"name": "k_step2d<32,8,true>", "bytes": 28 * pts, "avg_s": a_avg,
+                    "total_s": a_avg * n_adj_launch, "launches": n_adj_launch}}
+    dom = max(kern, key=lambda k: kern[k]["total_s"])
+    kd = kern[dom]
+    achieved = kd["bytes"] / kd["avg_s"] / 1e9 if kd["avg_s"] > 0 else None
+    tr = TRAFFIC.get((kd["name"], kernel_hash()))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": tr,
+                "kernel": kd["name"], "peak_kind": peak_kind,
+                "bytes_per_launch": kd["bytes"], "avg_launch_us": kd["avg_s"] * 1e6,
+                "other": {k: {"kernel": v["name"], "avg_launch_us": v["avg_s"] * 1e6,
+                              "achieved_gbs": v["bytes"] / v["avg_s"] / 1e9 if v["avg_s"] else None,
+                              "share_of_timed_region": v["total_s"] / sec if sec else None}
+                          for k, v in kern.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nshot_per_gpu": p.nshot, "nt": p.nt, "grid": f"{p.nx}x{p.nz}",
+                       "padded_points": N, "store": "checkpoint", "nsnap": args.nsnap,
+                       "forward_steps_per_gradient": sched_steps,
+                       "l2": "inputs larger than L2 (d_obs %.0f MB, checkpoints %.1f GB per GPU)" % (
+                           d_obs.numel() * 4 / 1e6, nbytes / 1e9),
+                       "parallelism": f"shots x{world}, gradient all-reduce" if world > 1 else "single GPU"},
+            "pt_updates_per_s": updates / sec,
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk.summary()}
+
+    if not args.only_main and rank == 0:
+        del work
+        torch.cuda.empty_cache()
+        # plain: one shot per call
+        nplain = min(4, p.nshot)
+        wb = wave.wave_workspace_size(grid, wave.OP_GRADIENT, p.src[:1], p.rec[:1], store, args.nsnap)
+        w1 = torch.empty(wb, dtype=torch.uint8, device=dev)
+        g1 = torch.empty_like(grad)
+
+        def plain(i):
+            wave.wave_gradient(grid, vel, p.src[i:i + 1], wavelet[i:i + 1], p.rec[i:i + 1], d_obs[i:i + 1],
+                               store=store, nsnap=args.nsnap, grad=g1, work=w1)
+
+        plain(0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(nplain):
+            plain(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["plain_shot_gradients_per_s"] = nplain / (e0.elapsed_time(e1) / 1e3)
+        del w1
+        torch.cuda.empty_cache()
+        # BF16 full storage
+        wb = wave.wave_workspace_size(grid, wave.OP_GRADIENT, p.src, p.rec, wave.STORE_BF16, 1)
+        wbf = torch.empty(wb, dtype=torch.uint8, device=dev)
+        g2 = torch.empty_like(grad)
+        wave.wave_gradient(grid, vel, p.src, wavelet, p.rec, d_obs, store=wave.STORE_BF16, grad=g2, work=wbf)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        nb = 2
+        for _ in range(nb):
+            wave.wave_gradient(grid, vel, p.src, wavelet, p.rec, d_obs, store=wave.STORE_BF16, grad=g2, work=wbf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["bf16_store_shot_gradients_per_s"] = nb * p.nshot / (e0.elapsed_time(e1) / 1e3)
+        line["bf16_store_vs_checkpoint_rel_l2"] = float((g2 - grad).norm() / grad.norm())
+        del wbf
+        torch.cuda.empty_cache()
+        # end to end through host buffers (pinned), same checkpointed gradient
+        work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        h_vel = vel.cpu().pin_memory()
+        h_wav = wavelet.cpu().pin_memory()
+        h_obs = d_obs.cpu().pin_memory()
+        h_grad = torch.empty(grid.phys_shape, dtype=torch.float32).pin_memory()
+        h2d = (h_vel.numel() + h_wav.numel() + h_obs.numel()) * 4
+        d2h = h_grad.numel() * 4 + 8
+
+        def e2e_step():
+            dv = h_vel.to(dev, non_blocking=True)
+            dw = h_wav.to(dev, non_blocking=True)
+            do = h_obs.to(dev, non_blocking=True)
+            phi, g, _ = wave.wave_gradient(grid, dv, p.src, dw, p.rec, do, store=store, nsnap=args.nsnap,
+                                           grad=grad, work=work)
+            h_grad.copy_(g, non_blocking=True)
+            torch.cuda.synchronize()
+            return phi
+
+        e2e_step()
+        t0 = time.perf_counter()
+        ne = max(2, args.steps // 2)
+        for _ in range(ne):
+            e2e_step()
+        el = time.perf_counter() - t0
+        line["e2e"] = {"value": ne * p.nshot / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h}
+        if world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(p.nt)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * wave.h -- C ABI of libwave: batched 2D/3D isotropic acoustic modelling, its
+ * adjoint and the FWI/RTM gradient on one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow arxiv 2304.05592 (Louboutin, Yin et al., "Learned
+ * multiphysics inversion with differentiable programming and machine
+ * learning"), section "Wave-equation-based inversion":
+ *   F(m) = P_r A(m)^{-1} P_s^T           (Eq. eq-fwi), m = squared slowness,
+ *   Phi(m) = 1/2 || F(m) q - d ||_2^2     (Eq. eq-fwi, the loss of the AD example),
+ *   grad Phi = J'(F(m) q - d)             (judiJacobian, "gradient w.r.t. squared slowness"),
+ *   F' dy                                 (pullback of the rrule for F*q).
+ * The paper leaves the discretisation open.  This library uses
+ *   (M+E) u^{n+1} = (2M + dt^2 L) u^n - (M-E) u^{n-1} + dt^2 S q^n,  u^{-1} = u^0 = 0,
+ *   d^n = R u^n  (n = 0 .. nt-1; d^0 is always zero),
+ * with M = diag(1/v^2) on a grid padded by nb sponge cells on every side (the
+ * model is copied outward from the nearest physical cell), E = diag(eta dt/2),
+ * eta = gamma0 (d/nb)^2 / vref^2 with d the depth into the sponge in cells and
+ * gamma0 = 3 vref ln(1000) / (2 nb h), L the 8th-order centred Laplacian with
+ * zero values beyond the padded grid, S bilinear (2D) or trilinear (3D)
+ * injection with weights w / h^ndim, R the same interpolation as sampling.
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are C order with x fastest: 2D velocity [nz][nx], 3D [nz][ny][nx].
+ *  - Coordinates are metres from the first physical grid point, ordered (x, z)
+ *    in 2D and (x, y, z) in 3D, and must lie inside the physical grid
+ *    (0 <= x <= (nx-1) h, ...); otherwise WAVE_ERR_GEOMETRY.
+ *  - "dev" pointers are CUDA device memory, "host" pointers are host memory.
+ *    The caller owns every buffer.  The library allocates nothing: all scratch
+ *    comes from the caller's workspace (size from wave_workspace_size).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is queued
+ *    on that stream; every call synchronises the stream once after its set-up
+ *    kernels (to validate the model against the stability limit before the
+ *    time loop) and once at its end (to read the device error word), so a call
+ *    returns with its results complete.
+ *  - Shot s uses sources src_xyz[s][0..nsrc) and receivers rec_xyz[s][0..nrec);
+ *    every shot shares the grid and the velocity model.
+ *  - Errors found before any launch (arguments, geometry, workspace size)
+ *    return without touching the outputs.  WAVE_ERR_CFL and
+ *    WAVE_ERR_NONFINITE are found after the set-up kernels and also leave the
+ *    outputs untouched.
+ */
+#ifndef WAVE_H
+#define WAVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WAVE_OK = 0,
+    WAVE_ERR_ARG = 1,       /* null pointer, negative count, bad grid, unknown mode */
+    WAVE_ERR_CFL = 2,       /* dt * vmax / h above 2 / sqrt(ndim * 2048/315)          */
+    WAVE_ERR_GEOMETRY = 3,  /* a source or receiver outside the physical grid         */
+    WAVE_ERR_WORKSPACE = 4, /* workspace null or smaller than wave_workspace_size     */
+    WAVE_ERR_CUDA = 5,      /* a CUDA runtime call or kernel launch failed            */
+    WAVE_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out (persistent launch) */
+    WAVE_ERR_NONFINITE = 7  /* velocity not finite and positive, or NaN in a result   */
+} wave_status_t;
+
+typedef struct {
+    int ndim;   /* 2 or 3                                                  */
+    int nx;     /* physical grid points along x (>= 2)                      */
+    int ny;     /* physical grid points along y (3D only, >= 2)             */
+    int nz;     /* physical grid points along z (>= 2)                      */
+    int nb;     /* sponge cells added outside the physical grid, each side  */
+    int nt;     /* time samples (>= 1); time step n is at t = n dt          */
+    float h;    /* grid spacing in metres, all axes                         */
+    float dt;   /* time step in seconds                                     */
+    float vref; /* sponge reference velocity in m/s (frozen, independent of
+                   the model); 0 disables damping                           */
+} wave_grid_t;
+
+/* How wave_gradient keeps the forward wavefield for the imaging condition. */
+typedef enum {
+    WAVE_STORE_CHECKPOINT = 0, /* binomial time checkpointing of FP32 states      */
+    WAVE_STORE_BF16 = 1,       /* every u^n stored in BF16 (round to nearest even) */
+    WAVE_STORE_FP32 = 2        /* every u^n stored in FP32 (exact, most memory)    */
+} wave_store_t;
+
+/* Bytes of device workspace that wave_forward (op 0), wave_adjoint (op 1) or
+ * wave_gradient (op 2) needs for this problem.  The coordinates (host, same
+ * layout as in the calls) are needed because interpolation taps of zero
+ * weight are dropped.  `store` and `nsnap` matter for op 2 only (nsnap =
+ * number of checkpoint slots, each holding two FP32 wavefields per shot; the
+ * library uses at most nt/2 of them: one per pair of time steps).  The workspace must be
+ * 256-byte aligned.  Host function, no device work. */
+wave_status_t wave_workspace_size(const wave_grid_t* grid, int op, int nshot, int nsrc, const float* src_xyz,
+                                  int nrec, const float* rec_xyz, int store, int nsnap,
+                                  size_t* bytes /* host out */);
+
+/* Forward modelling d = F(m) q (Eq. eq-fwi, P_r A(m)^{-1} P_s^T).
+ *   vel      dev  [nz][(ny)][nx] velocity (m/s)
+ *   src_xyz  host [nshot][nsrc][ndim] source coordinates
+ *   wavelet  dev  [nshot][nt][nsrc] source time functions q
+ *   rec_xyz  host [nshot][nrec][ndim] receiver coordinates
+ *   data     dev  out [nshot][nt][nrec] shot records (row n = 0 is zero) */
+wave_status_t wave_forward(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
+                           const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
+                           float* data, void* work, size_t work_bytes, void* stream);
+
+/* Adjoint in the source, F(m)' r (the pullback of the rrule for F*q):
+ *   (F' r)^n = dt^2 S' mu^{n+1} for n = 0..nt-2 and 0 at n = nt-1, where
+ *   (M+E) mu^k = (2M + dt^2 L) mu^{k+1} - (M-E) mu^{k+2} + R' r^k, k = nt-1..1.
+ *   resid    dev  [nshot][nt][nrec] data-space input r
+ *   src_out  dev  out [nshot][nt][nsrc] */
+wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
+                           const float* src_xyz, int nrec, const float* rec_xyz, const float* resid,
+                           float* src_out, void* work, size_t work_bytes, void* stream);
+
+/* FWI gradient (judiJacobian(F, q)' * (F q - d), i.e. J' applied to the data
+ * residual) of Phi(m) = 1/2 sum_s ||F_s(m) q_s - d_s||^2 with respect to the
+ * physical squared slowness m = 1/v^2, summed over shots:
+ *   grad_pad = - sum_n mu^{n+1} .* (u^{n+1} - 2 u^n + u^{n-1})  (zero-lag
+ *   cross-correlation of the adjoint field with the second time difference of
+ *   the forward field), then summed back onto the physical cells the padded
+ *   model was copied from.
+ *   d_obs    dev  [nshot][nt][nrec] observed data
+ *   grad     dev  out [nz][(ny)][nx] dPhi/dm
+ *   d_syn    dev  out [nshot][nt][nrec] synthetic data, or NULL
+ *   misfit   host out Phi (double), or NULL
+ *   store    a wave_store_t; nsnap = checkpoint slots (CHECKPOINT only, >= 1) */
+wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
+                            const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
+                            const float* d_obs, float* grad, float* d_syn, double* misfit, int store,
+                            int nsnap, void* work, size_t work_bytes, void* stream);
+
+/* Ricker wavelet q(t_n) = (1 - 2 a) exp(-a), a = (pi f0 (n dt - 1/f0))^2,
+ * n = 0..nt-1 (the wavelet of the paper's FWI example, peak delayed by 1/f0).
+ *   out dev out [nt] */
+wave_status_t wave_ricker(float f0, float dt, int nt, float* out, void* stream);
+
+/* The binomial checkpoint schedule that wave_gradient runs in
+ * WAVE_STORE_CHECKPOINT mode (Griewank and Walther's optimal reversal with a
+ * fixed number of snapshots; the paper itself only needs J' and leaves the
+ * memory strategy open).  Host function, no device work.
+ *   fwd_steps host out: forward time steps executed, first sweep included
+ *   actions   host out [capacity][3]: (kind, arg, state) per action with kind
+ *             0 advance (arg = start state, state = end state), 1 save
+ *             (arg = slot), 2 restore (arg = slot, -1 = zero state), 3 adjoint
+ *             steps state and state-1 (arg = state), 4 data complete;
+ *             state j stands for (u^j, u^{j-1})
+ *   nactions  host out: total number of actions (may exceed capacity) */
+wave_status_t wave_checkpoint_schedule(int nt, int nsnap, long long* fwd_steps, int* actions, int capacity,
+                                       int* nactions);
+
+/* Measurement support (no counterpart in the paper).
+ * wave_launch_count: number of kernels this library has launched so far in
+ * the process.  wave_profile_start(every): from now on, bracket every
+ * `every`-th stencil time-step launch with two CUDA events on its stream
+ * (at most 8192 samples).  wave_profile_stop: stops sampling, waits for the
+ * sampled events and returns the summed milliseconds and the number of
+ * sampled forward and adjoint step launches (any pointer may be NULL). */
+long long wave_launch_count(void);
+wave_status_t wave_profile_start(int every);
+wave_status_t wave_profile_stop(double* fwd_ms, long long* fwd_n, double* adj_ms, long long* adj_n);
+
+/* Largest stable dt * vmax / h for ndim = 2 or 3 (0 for other ndim). */
+double wave_courant_limit(int ndim);
+
+/* Static text for a status code. */
+const char* wave_status_str(wave_status_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WAVE_H */

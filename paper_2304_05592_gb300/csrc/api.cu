@@ -1,0 +1,574 @@
+// api.cu -- the extern "C" entry points of libwave and the host orchestration
+// of the time loops (forward sweep, adjoint sweep, checkpointed reversal).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+using namespace wave;
+
+namespace {
+
+constexpr int kNumPartials = 1024;
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t n)
+    {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+struct DevTaps {
+    TapList l;
+    int *tile_start = nullptr, *idx = nullptr, *ab = nullptr, *slot = nullptr, *pt_start = nullptr;
+    float *fac = nullptr, *gw = nullptr, *w = nullptr;
+    std::vector<float> gw_host;
+};
+
+struct Layout {
+    Dims d;
+    Tiling t;
+    int op = 0, nshot = 0, nsrc = 0, nrec = 0, store = 0, nsnap = 0;
+    HostTaps hs, hr;
+    DevTaps ts, tr;
+    int* err = nullptr;
+    float* vmax = nullptr;
+    double* part = nullptr;
+    double* misfit = nullptr;
+    float* kap = nullptr;
+    float* W[2] = {nullptr, nullptr};
+    float* A[2] = {nullptr, nullptr};
+    float* gacc = nullptr;
+    float* slots_rec = nullptr;
+    float* slots_src = nullptr;
+    float* dsyn = nullptr;
+    float* snaps = nullptr;
+    __nv_bfloat16* st16 = nullptr;
+    float* st32 = nullptr;
+    size_t bytes = 0;
+};
+
+bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
+
+wave_status_t check_grid(const wave_grid_t* g)
+{
+    if (!g) return WAVE_ERR_ARG;
+    if (g->ndim != 2 && g->ndim != 3) return WAVE_ERR_ARG;
+    if (g->nx < 2 || g->nz < 2 || (g->ndim == 3 && g->ny < 2)) return WAVE_ERR_ARG;
+    if (g->nb < 0 || g->nt < 1) return WAVE_ERR_ARG;
+    if (!finite_pos(g->h) || !finite_pos(g->dt) || !isfinite(g->vref) || g->vref < 0.0f) return WAVE_ERR_ARG;
+    const Dims d = make_dims(*g);
+    if (d.cell >= (1LL << 31)) return WAVE_ERR_ARG;  // flat indices are 32-bit
+    return WAVE_OK;
+}
+
+void carve_taps(Carver& c, const HostTaps& h, long long ntiles_all, DevTaps& t)
+{
+    const size_t ntap = h.idx.size();
+    t.tile_start = c.take<int>(ntiles_all + 1);
+    t.idx = c.take<int>(ntap);
+    t.fac = c.take<float>(ntap);
+    t.gw = c.take<float>(ntap);
+    t.ab = c.take<int>(ntap);
+    t.slot = c.take<int>(ntap);
+    t.w = c.take<float>(ntap);
+    t.pt_start = c.take<int>(h.pt_start.size());
+    t.l.tile_start = t.tile_start;
+    t.l.idx = t.idx;
+    t.l.fac = t.fac;
+    t.l.gw = t.gw;
+    t.l.ab = t.ab;
+    t.l.slot = t.slot;
+    t.l.w = t.w;
+    t.l.pt_start = t.pt_start;
+    t.l.npts = h.npts;
+    t.l.ntap = (int)ntap;
+}
+
+int macro_count(int nt)
+{
+    const int K = nt - 1;
+    if (K < 1) return 0;
+    const int jmin = (K % 2 == 1) ? 1 : 2;
+    return (K - jmin) / 2 + 1;
+}
+
+// Builds the tap tables and carves the workspace (base may be NULL to size it).
+wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const float* src_xyz, int nrec,
+                   const float* rec_xyz, int store, int nsnap, void* base, Layout& L)
+{
+    wave_status_t st = check_grid(g);
+    if (st) return st;
+    if (op < 0 || op > 2 || nshot < 0 || nsrc < 0 || nrec < 0) return WAVE_ERR_ARG;
+    if ((nshot && nsrc && !src_xyz) || (nshot && nrec && !rec_xyz)) return WAVE_ERR_ARG;
+    if (op == 2 && (store < 0 || store > 2 || (store == WAVE_STORE_CHECKPOINT && nsnap < 1))) return WAVE_ERR_ARG;
+    if ((long long)nshot * g->nt * std::max(nsrc, nrec) >= (1LL << 31)) return WAVE_ERR_ARG;
+    L.d = make_dims(*g);
+    L.t = choose_tiling(L.d, nshot);
+    L.op = op;
+    L.nshot = nshot;
+    L.nsrc = nsrc;
+    L.nrec = nrec;
+    L.store = store;
+    const Dims& d = L.d;
+    st = build_taps(d, L.t, nshot, nsrc, src_xyz, L.hs);
+    if (st) return st;
+    st = build_taps(d, L.t, nshot, nrec, rec_xyz, L.hr);
+    if (st) return st;
+
+    const long long ntiles_all = (long long)nshot * L.t.tiles_per_shot();
+    const size_t field = (size_t)nshot * d.cell;
+    const size_t nt = (size_t)d.nt;
+    Carver c(base);
+    L.err = c.take<int>(4);
+    L.vmax = c.take<float>(1);
+    L.part = c.take<double>(kNumPartials);
+    L.misfit = c.take<double>(1);
+    L.kap = c.take<float>(d.cell);
+    carve_taps(c, L.hs, ntiles_all, L.ts);
+    carve_taps(c, L.hr, ntiles_all, L.tr);
+    if (op == 0 || op == 2) {
+        L.W[0] = c.take<float>(field);
+        L.W[1] = c.take<float>(field);
+        L.slots_rec = c.take<float>(nt * L.hr.idx.size());
+    }
+    if (op == 1 || op == 2) {
+        L.A[0] = c.take<float>(field);
+        L.A[1] = c.take<float>(field);
+    }
+    if (op == 1) L.slots_src = c.take<float>(nt * L.hs.idx.size());
+    if (op == 2) {
+        L.gacc = c.take<float>(field);
+        L.dsyn = c.take<float>((size_t)nshot * nt * nrec);
+        if (store == WAVE_STORE_CHECKPOINT) {
+            L.nsnap = std::max(0, std::min(nsnap, macro_count(d.nt)));
+            L.snaps = c.take<float>((size_t)L.nsnap * 2 * field);
+        } else if (store == WAVE_STORE_BF16) {
+            L.st16 = c.take<__nv_bfloat16>(nt * field);
+        } else {
+            L.st32 = c.take<float>(nt * field);
+        }
+    }
+    L.bytes = c.off;
+    // Gather weights: receivers sample with w; the source-side adjoint
+    // gathers dt^2 w / h^ndim (the transpose of the injection).
+    const double hd = d.ndim == 3 ? (double)d.h * d.h * d.h : (double)d.h * d.h;
+    L.tr.gw_host.assign(L.hr.w.begin(), L.hr.w.end());
+    L.ts.gw_host.resize(L.hs.w.size());
+    for (size_t j = 0; j < L.hs.w.size(); ++j) L.ts.gw_host[j] = (float)(L.hs.w[j] * (double)d.dt * d.dt / hd);
+    return WAVE_OK;
+}
+
+#define CK(x)                                 \
+    do {                                      \
+        if ((x) != cudaSuccess) {             \
+            (void)cudaGetLastError();         \
+            return WAVE_ERR_CUDA;             \
+        }                                     \
+    } while (0)
+
+wave_status_t upload_taps(const HostTaps& h, DevTaps& t, cudaStream_t s)
+{
+    const size_t ntap = h.idx.size();
+    CK(cudaMemcpyAsync(t.tile_start, h.tile_start.data(), h.tile_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.pt_start, h.pt_start.data(), h.pt_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (ntap) {
+        CK(cudaMemcpyAsync(t.idx, h.idx.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(t.ab, h.ab.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(t.slot, h.slot.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(t.w, h.w.data(), ntap * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(t.gw, t.gw_host.data(), ntap * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    return WAVE_OK;
+}
+
+double courant_limit(int ndim)
+{
+    // 2048/315 is the largest magnitude of the 1D 8th-order symbol (at the
+    // Nyquist wavenumber); leapfrog is stable for ndim K (v dt / h)^2 <= 4.
+    if (ndim != 2 && ndim != 3) return 0.0;
+    return 2.0 / sqrt(ndim * 2048.0 / 315.0);
+}
+
+// c_eps such that eps = kap * c_eps * depth^2 equals eta dt v^2 / 2 with
+// eta = gamma0 (depth/nb)^2 / vref^2, gamma0 = 3 vref ln(1000) / (2 nb h).
+float sponge_coefficient(const Dims& d)
+{
+    if (d.nb == 0 || d.vref <= 0.0f) return 0.0f;
+    const double nb = d.nb;
+    return (float)(3.0 * log(1000.0) * d.h / (4.0 * d.dt * d.vref * nb * nb * nb));
+}
+
+// Uploads tables, prepares the model, validates it and fills the injection factors.
+wave_status_t setup(Layout& L, const float* vel, cudaStream_t s)
+{
+    wave_status_t st = upload_taps(L.hs, L.ts, s);
+    if (st) return st;
+    st = upload_taps(L.hr, L.tr, s);
+    if (st) return st;
+    CK(cudaMemsetAsync(L.err, 0, 4 * sizeof(int), s));
+    CK(cudaMemsetAsync(L.vmax, 0, sizeof(float), s));
+    launch_prep(L.d, vel, L.kap, L.vmax, L.err, s);
+    CK(cudaGetLastError());
+    int herr = 0;
+    float hvmax = 0.0f;
+    CK(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hvmax, L.vmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr & kErrNonFinite) return WAVE_ERR_NONFINITE;
+    if ((double)L.d.dt * hvmax / L.d.h > courant_limit(L.d.ndim)) return WAVE_ERR_CFL;
+    const float ceps = sponge_coefficient(L.d);
+    const double h = L.d.h, dt = L.d.dt;
+    // Forward source injection adds dt^2 w q / (h^ndim (m + e)) = kap h^(2-ndim) w q / (1 + eps).
+    launch_tapfac(L.d, L.ts.l, L.kap, (float)(L.d.ndim == 3 ? 1.0 / h : 1.0), ceps, s);
+    // Adjoint receiver injection adds w r / (m + e) = kap (h/dt)^2 w r / (1 + eps).
+    launch_tapfac(L.d, L.tr.l, L.kap, (float)(h * h / (dt * dt)), ceps, s);
+    CK(cudaGetLastError());
+    return WAVE_OK;
+}
+
+StepArgs base_args(const Layout& L)
+{
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    const Dims& d = L.d;
+    a.kap = L.kap;
+    a.Nx = d.Nx;
+    a.Ny = d.Ny;
+    a.Nz = d.Nz;
+    a.P = d.P;
+    a.cell = d.cell;
+    a.nb = d.nb;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.ceps = sponge_coefficient(d);
+    a.ntx = L.t.ntx;
+    a.nty = L.t.nty;
+    a.ntz = L.t.ntz;
+    a.err = L.err;
+    return a;
+}
+
+// Forward step n: u^{n+1} into `unew` (which holds u^{n-1}), injecting q^n;
+// optionally records d^{n+1} and stores u^{n+1}.
+void fwd_step(const Layout& L, const float* u, float* unew, int n, const float* wavelet, bool record,
+              __nv_bfloat16* st16, float* st32, cudaStream_t s)
+{
+    StepArgs a = base_args(L);
+    a.u = u;
+    a.unew = unew;
+    if (L.nsrc > 0 && L.ts.l.ntap > 0) {
+        a.inj = L.ts.l;
+        a.amp_a = wavelet;
+        a.amp_row = n;
+    }
+    if (record && L.nrec > 0 && L.tr.l.ntap > 0) {
+        a.gat = L.tr.l;
+        a.slots = L.slots_rec;
+        a.slot_row = n + 1;
+    }
+    a.st16 = st16;
+    a.st32 = st32;
+    launch_step(L.t, L.d.ndim, false, L.nshot, a, s);
+}
+
+// Adjoint step k: mu^k into `mu0` (which holds mu^{k+2}), injecting
+// amp_a - amp_b at time k at the receivers; optionally gathers the source-side
+// adjoint (F' r)^{k-1} and accumulates the imaging condition with u^k.
+void adj_step(const Layout& L, const float* mu1, float* mu0, int k, const float* amp_a, const float* amp_b,
+              bool gather_src, const float* uf32, const __nv_bfloat16* uf16, float* gacc, cudaStream_t s)
+{
+    StepArgs a = base_args(L);
+    a.u = mu1;
+    a.unew = mu0;
+    if (L.nrec > 0 && L.tr.l.ntap > 0) {
+        a.inj = L.tr.l;
+        a.amp_a = amp_a;
+        a.amp_b = amp_b;
+        a.amp_row = k;
+    }
+    if (gather_src && L.nsrc > 0 && L.ts.l.ntap > 0) {
+        a.gat = L.ts.l;
+        a.slots = L.slots_src;
+        a.slot_row = k - 1;
+    }
+    a.uf32 = uf32;
+    a.uf16 = uf16;
+    a.gacc = gacc;
+    launch_step(L.t, L.d.ndim, true, L.nshot, a, s);
+}
+
+wave_status_t finish(const Layout& L, cudaStream_t s)
+{
+    CK(cudaGetLastError());
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr & kErrTimeout) return WAVE_ERR_TIMEOUT;
+    if (herr & kErrNonFinite) return WAVE_ERR_NONFINITE;
+    if (herr) return WAVE_ERR_CUDA;
+    return WAVE_OK;
+}
+
+wave_status_t check_work(const Layout& L, void* work, size_t work_bytes)
+{
+    if (L.bytes > 0 && (!work || work_bytes < L.bytes)) return WAVE_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(work) % 256) return WAVE_ERR_WORKSPACE;
+    return WAVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wave_status_str(wave_status_t s)
+{
+    switch (s) {
+    case WAVE_OK: return "ok";
+    case WAVE_ERR_ARG: return "invalid argument";
+    case WAVE_ERR_CFL: return "time step above the stability limit";
+    case WAVE_ERR_GEOMETRY: return "source or receiver outside the physical grid";
+    case WAVE_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case WAVE_ERR_CUDA: return "CUDA error";
+    case WAVE_ERR_TIMEOUT: return "device-side wait timed out";
+    case WAVE_ERR_NONFINITE: return "non-finite or non-positive value";
+    }
+    return "unknown status";
+}
+
+double wave_courant_limit(int ndim) { return courant_limit(ndim); }
+
+wave_status_t wave_workspace_size(const wave_grid_t* grid, int op, int nshot, int nsrc, const float* src_xyz,
+                                  int nrec, const float* rec_xyz, int store, int nsnap, size_t* bytes)
+{
+    if (!bytes) return WAVE_ERR_ARG;
+    Layout L;
+    wave_status_t st = plan(grid, op, nshot, nsrc, src_xyz, nrec, rec_xyz, store, nsnap, nullptr, L);
+    if (st) return st;
+    *bytes = L.bytes;
+    return WAVE_OK;
+}
+
+wave_status_t wave_forward(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                           const float* wavelet, int nrec, const float* rec_xyz, float* data, void* work,
+                           size_t work_bytes, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    wave_status_t st = plan(grid, 0, nshot, nsrc, src_xyz, nrec, rec_xyz, 0, 0, work, L);
+    if (st) return st;
+    if (nshot == 0) return WAVE_OK;
+    if (!vel || (nsrc && !wavelet) || (nrec && !data)) return WAVE_ERR_ARG;
+    if ((st = check_work(L, work, work_bytes))) return st;
+    if ((st = setup(L, vel, s))) return st;
+    const size_t fb = (size_t)nshot * L.d.cell * sizeof(float);
+    CK(cudaMemsetAsync(L.W[0], 0, fb, s));
+    CK(cudaMemsetAsync(L.W[1], 0, fb, s));
+    const size_t nrow = L.hr.idx.size();
+    if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
+    int cur = 0;
+    for (int n = 0; n + 1 < L.d.nt; ++n) {
+        fwd_step(L, L.W[cur], L.W[1 - cur], n, wavelet, true, nullptr, nullptr, s);
+        cur ^= 1;
+    }
+    if (nrec) {
+        launch_finalize(L.tr.l, L.slots_rec, nshot, L.d.nt, data, s);
+        launch_nan_scan(data, (long long)nshot * L.d.nt * nrec, L.err, s);
+    }
+    return finish(L, s);
+}
+
+wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                           int nrec, const float* rec_xyz, const float* resid, float* src_out, void* work,
+                           size_t work_bytes, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    wave_status_t st = plan(grid, 1, nshot, nsrc, src_xyz, nrec, rec_xyz, 0, 0, work, L);
+    if (st) return st;
+    if (nshot == 0) return WAVE_OK;
+    if (!vel || (nrec && !resid) || (nsrc && !src_out)) return WAVE_ERR_ARG;
+    if ((st = check_work(L, work, work_bytes))) return st;
+    if ((st = setup(L, vel, s))) return st;
+    const size_t fb = (size_t)nshot * L.d.cell * sizeof(float);
+    CK(cudaMemsetAsync(L.A[0], 0, fb, s));
+    CK(cudaMemsetAsync(L.A[1], 0, fb, s));
+    const size_t nrow = L.hs.idx.size();
+    if (nrow) CK(cudaMemsetAsync(L.slots_src + (size_t)(L.d.nt - 1) * nrow, 0, nrow * sizeof(float), s));
+    int cur = 0;
+    for (int k = L.d.nt - 1; k >= 1; --k) {
+        adj_step(L, L.A[cur], L.A[1 - cur], k, resid, nullptr, true, nullptr, nullptr, nullptr, s);
+        cur ^= 1;
+    }
+    if (nsrc) {
+        launch_finalize(L.ts.l, L.slots_src, nshot, L.d.nt, src_out, s);
+        launch_nan_scan(src_out, (long long)nshot * L.d.nt * nsrc, L.err, s);
+    }
+    return finish(L, s);
+}
+
+wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                            const float* wavelet, int nrec, const float* rec_xyz, const float* d_obs, float* grad,
+                            float* d_syn, double* misfit, int store, int nsnap, void* work, size_t work_bytes,
+                            void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    wave_status_t st = plan(grid, 2, nshot, nsrc, src_xyz, nrec, rec_xyz, store, nsnap, work, L);
+    if (st) return st;
+    if (!vel || !grad || (nshot && nsrc && !wavelet) || (nshot && nrec && !d_obs)) return WAVE_ERR_ARG;
+    if ((st = check_work(L, work, work_bytes))) return st;
+    const Dims& d = L.d;
+    if (nshot == 0) {
+        CK(cudaMemsetAsync(grad, 0, d.phys * sizeof(float), s));
+        CK(cudaStreamSynchronize(s));
+        if (misfit) *misfit = 0.0;
+        return WAVE_OK;
+    }
+    if ((st = setup(L, vel, s))) return st;
+    const size_t field = (size_t)nshot * d.cell;
+    const size_t fb = field * sizeof(float);
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaMemsetAsync(L.W[i], 0, fb, s));
+        CK(cudaMemsetAsync(L.A[i], 0, fb, s));
+    }
+    CK(cudaMemsetAsync(L.gacc, 0, fb, s));
+    const size_t nrow = L.hr.idx.size();
+    if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
+    const long long ndata = (long long)nshot * d.nt * nrec;
+    const int K = d.nt - 1;
+
+    auto finalize_data = [&]() {
+        if (nrec) {
+            launch_finalize(L.tr.l, L.slots_rec, nshot, d.nt, L.dsyn, s);
+            launch_misfit(L.dsyn, d_obs, ndata, L.part, kNumPartials, L.misfit, s);
+        } else {
+            cudaMemsetAsync(L.misfit, 0, sizeof(double), s);
+        }
+    };
+
+    if (store != WAVE_STORE_CHECKPOINT) {
+        if (L.st16) CK(cudaMemsetAsync(L.st16, 0, field * sizeof(__nv_bfloat16), s));
+        if (L.st32) CK(cudaMemsetAsync(L.st32, 0, fb, s));
+        int cur = 0;
+        for (int n = 0; n < K; ++n) {
+            __nv_bfloat16* r16 = L.st16 ? L.st16 + (size_t)(n + 1) * field : nullptr;
+            float* r32 = L.st32 ? L.st32 + (size_t)(n + 1) * field : nullptr;
+            fwd_step(L, L.W[cur], L.W[1 - cur], n, wavelet, true, r16, r32, s);
+            cur ^= 1;
+        }
+        finalize_data();
+        int acur = 0;
+        for (int k = K; k >= 1; --k) {
+            const __nv_bfloat16* u16 = L.st16 ? L.st16 + (size_t)k * field : nullptr;
+            const float* u32 = L.st32 ? L.st32 + (size_t)k * field : nullptr;
+            adj_step(L, L.A[acur], L.A[1 - acur], k, L.dsyn, d_obs, false, u32, u16, L.gacc, s);
+            acur ^= 1;
+        }
+    } else if (K < 1) {
+        finalize_data();
+    } else {
+        const Schedule sch = make_schedule(d.nt, L.nsnap);
+        int wcur = 0, wstate = 0, recorded = 0, acur = 0;
+        for (const Action& act : sch.actions) {
+            switch (act.kind) {
+            case kAdvance: {
+                const int j0 = sch.state_of(act.a), j1 = sch.state_of(act.b);
+                if (j0 != wstate) return WAVE_ERR_ARG;  // schedule inconsistency (not reachable)
+                for (int n = j0; n < j1; ++n) {
+                    const bool rec = n >= recorded;
+                    fwd_step(L, L.W[wcur], L.W[1 - wcur], n, wavelet, rec, nullptr, nullptr, s);
+                    if (rec) recorded = n + 1;
+                    wcur ^= 1;
+                }
+                wstate = j1;
+                break;
+            }
+            case kSave: {
+                float* slot = L.snaps + (size_t)act.a * 2 * field;
+                CK(cudaMemcpyAsync(slot, L.W[wcur], fb, cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(slot + field, L.W[1 - wcur], fb, cudaMemcpyDeviceToDevice, s));
+                break;
+            }
+            case kRestore: {
+                if (act.a < 0) {
+                    CK(cudaMemsetAsync(L.W[0], 0, fb, s));
+                    CK(cudaMemsetAsync(L.W[1], 0, fb, s));
+                } else {
+                    const float* slot = L.snaps + (size_t)act.a * 2 * field;
+                    CK(cudaMemcpyAsync(L.W[0], slot, fb, cudaMemcpyDeviceToDevice, s));
+                    CK(cudaMemcpyAsync(L.W[1], slot + field, fb, cudaMemcpyDeviceToDevice, s));
+                }
+                wcur = 0;
+                wstate = sch.state_of(act.b);
+                break;
+            }
+            case kFinalize:
+                if (recorded != K) return WAVE_ERR_ARG;  // not reachable
+                finalize_data();
+                break;
+            case kAdjointPair: {
+                const int j = sch.state_of(act.a);
+                if (j != wstate) return WAVE_ERR_ARG;  // not reachable
+                adj_step(L, L.A[acur], L.A[1 - acur], j, L.dsyn, d_obs, false, L.W[wcur], nullptr, L.gacc, s);
+                acur ^= 1;
+                if (j - 1 >= 1) {
+                    adj_step(L, L.A[acur], L.A[1 - acur], j - 1, L.dsyn, d_obs, false, L.W[1 - wcur], nullptr,
+                             L.gacc, s);
+                    acur ^= 1;
+                }
+                break;
+            }
+            }
+        }
+    }
+    launch_grad_reduce(d, L.gacc, nshot, grad, s);
+    launch_nan_scan(grad, d.phys, L.err, s);
+    if (d_syn && ndata) CK(cudaMemcpyAsync(d_syn, L.dsyn, ndata * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    double hm = 0.0;
+    CK(cudaMemcpyAsync(&hm, L.misfit, sizeof(double), cudaMemcpyDeviceToHost, s));
+    st = finish(L, s);
+    if (st == WAVE_OK && misfit) *misfit = hm;
+    return st;
+}
+
+wave_status_t wave_ricker(float f0, float dt, int nt, float* out, void* stream)
+{
+    if (!(f0 > 0.0f) || !(dt > 0.0f) || nt < 0 || (nt && !out)) return WAVE_ERR_ARG;
+    if (nt == 0) return WAVE_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_ricker(f0, dt, nt, out, s);
+    CK(cudaGetLastError());
+    return WAVE_OK;
+}
+
+wave_status_t wave_checkpoint_schedule(int nt, int nsnap, long long* fwd_steps, int* actions, int capacity,
+                                       int* nactions)
+{
+    if (nt < 1 || nsnap < 0) return WAVE_ERR_ARG;
+    const Schedule sch = make_schedule(nt, nsnap);
+    if (fwd_steps) *fwd_steps = sch.fwd_steps;
+    if (nactions) *nactions = (int)sch.actions.size();
+    if (actions) {
+        const int n = std::min<int>(capacity, (int)sch.actions.size());
+        for (int i = 0; i < n; ++i) {
+            const Action& a = sch.actions[i];
+            actions[3 * i] = a.kind;
+            actions[3 * i + 1] = a.kind == kAdvance || a.kind == kAdjointPair ? sch.state_of(a.a) : a.a;
+            actions[3 * i + 2] = a.kind == kFinalize ? 0 : sch.state_of(a.b);
+        }
+    }
+    return WAVE_OK;
+}
+
+}  // extern "C"

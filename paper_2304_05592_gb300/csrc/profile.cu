@@ -1,0 +1,106 @@
+// profile.cu -- launch counting and sampled CUDA-event timing of the stencil
+// kernels.  Off by default; wave_profile_start/stop bracket a measured region.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace wave {
+namespace {
+
+struct Sample {
+    cudaEvent_t start, stop;
+    bool adjoint;
+};
+
+std::atomic<long long> g_launches{0};
+std::mutex g_mu;
+bool g_on = false;
+int g_every = 1;
+long long g_seen = 0;
+std::vector<Sample> g_samples;  // recorded during the current region
+std::vector<cudaEvent_t> g_pool;
+size_t g_pool_next = 0;
+constexpr size_t kMaxSamples = 8192;
+
+cudaEvent_t take_event()
+{
+    if (g_pool_next == g_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g_pool.push_back(e);
+    }
+    return g_pool[g_pool_next++];
+}
+
+}  // namespace
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool profile_sample(bool adjoint, cudaStream_t s, cudaEvent_t* stop)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_on) return false;
+    const bool take = (g_seen++ % g_every) == 0 && g_samples.size() < kMaxSamples;
+    if (!take) return false;
+    Sample smp;
+    smp.start = take_event();
+    smp.stop = take_event();
+    smp.adjoint = adjoint;
+    if (!smp.start || !smp.stop) return false;
+    cudaEventRecord(smp.start, s);
+    g_samples.push_back(smp);
+    *stop = smp.stop;
+    return true;
+}
+
+void profile_close(cudaEvent_t stop, cudaStream_t s) { cudaEventRecord(stop, s); }
+
+}  // namespace wave
+
+using namespace wave;
+
+extern "C" {
+
+long long wave_launch_count(void) { return g_launches.load(); }
+
+wave_status_t wave_profile_start(int every)
+{
+    if (every < 1) return WAVE_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_on = true;
+    g_every = every;
+    g_seen = 0;
+    g_samples.clear();
+    g_pool_next = 0;
+    return WAVE_OK;
+}
+
+wave_status_t wave_profile_stop(double* fwd_ms, long long* fwd_n, double* adj_ms, long long* adj_n)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_on = false;
+    double f = 0.0, a = 0.0;
+    long long nf = 0, na = 0;
+    for (const Sample& smp : g_samples) {
+        if (cudaEventSynchronize(smp.stop) != cudaSuccess) return WAVE_ERR_CUDA;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, smp.start, smp.stop) != cudaSuccess) return WAVE_ERR_CUDA;
+        if (smp.adjoint) {
+            a += ms;
+            ++na;
+        } else {
+            f += ms;
+            ++nf;
+        }
+    }
+    g_samples.clear();
+    if (fwd_ms) *fwd_ms = f;
+    if (fwd_n) *fwd_n = nf;
+    if (adj_ms) *adj_ms = a;
+    if (adj_n) *adj_n = na;
+    return WAVE_OK;
+}
+
+}  // extern "C"

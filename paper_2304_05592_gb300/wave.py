@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libwave's C ABI (``include/wave.h``).
+
+The functions keep the C names and only marshal arguments: device arrays are
+torch CUDA tensors (float32, contiguous), coordinates are host arrays, the
+workspace is a torch uint8 tensor from torch's caching allocator, and the
+stream is torch's current stream unless one is given.  Every computation runs
+in libwave's CUDA kernels; there is no CPU path.  If the library has not been
+built, or a tensor is not on a CUDA device, the call raises.
+
+Operations (arxiv 2304.05592, "Wave-equation-based inversion", Eq. eq-fwi):
+``wave_forward`` is F(m) q = P_r A(m)^{-1} P_s^T q, ``wave_adjoint`` is the
+pullback F' r of the AD rule for F*q, ``wave_gradient`` returns the misfit
+1/2 ||F(m) q - d||^2 and J'(F(m) q - d), its gradient w.r.t. the squared
+slowness m.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libwave.so")
+
+STORE_CHECKPOINT, STORE_BF16, STORE_FP32 = 0, 1, 2
+OP_FORWARD, OP_ADJOINT, OP_GRADIENT = 0, 1, 2
+STATUS = {0: "WAVE_OK", 1: "WAVE_ERR_ARG", 2: "WAVE_ERR_CFL", 3: "WAVE_ERR_GEOMETRY",
+          4: "WAVE_ERR_WORKSPACE", 5: "WAVE_ERR_CUDA", 6: "WAVE_ERR_TIMEOUT", 7: "WAVE_ERR_NONFINITE"}
+
+
+class WaveError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = _lib().wave_status_str(status).decode() if _LIB is not None else ""
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({msg})")
+
+
+class wave_grid_t(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nb", ctypes.c_int), ("nt", ctypes.c_int), ("h", ctypes.c_float), ("dt", ctypes.c_float),
+                ("vref", ctypes.c_float)]
+
+
+_LIB = None
+EXPORTS = ("wave_workspace_size", "wave_forward", "wave_adjoint", "wave_gradient", "wave_ricker",
+           "wave_checkpoint_schedule", "wave_profile_start", "wave_profile_stop", "wave_courant_limit",
+           "wave_status_str", "wave_launch_count")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _lib():
+    """Loads libwave.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libwave.so is not built ({_LIB_PATH}); run __graft_entry__.build() "
+                               "or python -m paper_2304_05592_gb300.build")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        G = ctypes.POINTER(wave_grid_t)
+        lib.wave_workspace_size.argtypes = [G, I, I, I, P, I, P, I, I, ctypes.POINTER(ctypes.c_size_t)]
+        lib.wave_forward.argtypes = [G, P, I, I, P, P, I, P, P, P, ctypes.c_size_t, P]
+        lib.wave_adjoint.argtypes = [G, P, I, I, P, I, P, P, P, P, ctypes.c_size_t, P]
+        lib.wave_gradient.argtypes = [G, P, I, I, P, P, I, P, P, P, P, ctypes.POINTER(ctypes.c_double), I, I, P,
+                                      ctypes.c_size_t, P]
+        lib.wave_ricker.argtypes = [ctypes.c_float, ctypes.c_float, I, P, P]
+        lib.wave_checkpoint_schedule.argtypes = [I, I, ctypes.POINTER(ctypes.c_longlong), P, I,
+                                                 ctypes.POINTER(ctypes.c_int)]
+        lib.wave_courant_limit.argtypes = [I]
+        lib.wave_courant_limit.restype = ctypes.c_double
+        lib.wave_status_str.argtypes = [I]
+        lib.wave_status_str.restype = ctypes.c_char_p
+        lib.wave_profile_start.argtypes = [I]
+        lib.wave_profile_stop.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+        lib.wave_launch_count.argtypes = []
+        lib.wave_launch_count.restype = ctypes.c_longlong
+        for name in EXPORTS[:-3]:
+            getattr(lib, name).restype = I
+        _LIB = lib
+    return _LIB
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Physical grid nx x (ny x) nz at spacing h, nb sponge cells per side, nt
+    samples at step dt, frozen sponge reference velocity vref (0: no damping)."""
+    ndim: int
+    nx: int
+    nz: int
+    h: float
+    dt: float
+    nt: int
+    nb: int = 40
+    ny: int = 1
+    vref: float = 0.0
+
+    def c(self) -> wave_grid_t:
+        return wave_grid_t(self.ndim, self.nx, self.ny if self.ndim == 3 else 1, self.nz, self.nb, self.nt,
+                           self.h, self.dt, self.vref)
+
+    @property
+    def phys_shape(self):
+        return (self.nz, self.ny, self.nx) if self.ndim == 3 else (self.nz, self.nx)
+
+    @staticmethod
+    def of(p) -> "Grid":
+        """Grid of a synth.Problem."""
+        return Grid(p.ndim, p.nx, p.nz, float(p.h), float(p.dt), int(p.nt), int(p.nb), int(p.ny), float(p.vref))
+
+
+def _dev(t: torch.Tensor, name: str, shape=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (libwave has no CPU path)")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _host_xyz(a, ndim: int) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if a.ndim != 3 or a.shape[-1] != ndim:
+        raise ValueError(f"coordinates must have shape [nshot][npts][{ndim}], got {a.shape}")
+    return a
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+def wave_workspace_size(grid: Grid, op: int, src_xyz, rec_xyz, store: int = STORE_CHECKPOINT,
+                        nsnap: int = 1) -> int:
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    out = ctypes.c_size_t(0)
+    g = grid.c()
+    st = _lib().wave_workspace_size(ctypes.byref(g), op, src.shape[0], src.shape[1], _ptr(src), rec.shape[1],
+                                    _ptr(rec), store, nsnap, ctypes.byref(out))
+    if st:
+        raise WaveError(st, "wave_workspace_size")
+    return int(out.value)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def wave_forward(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, data=None,
+                 stream=None) -> torch.Tensor:
+    """Shot records [nshot][nt][nrec] = F(m) q for every shot."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    if rec.shape[0] != ns:
+        raise ValueError("src_xyz and rec_xyz disagree on the number of shots")
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pw = _dev(wavelet, "wavelet", (ns, grid.nt, nsrc))
+    if data is None:
+        data = torch.empty((ns, grid.nt, nrec), dtype=torch.float32, device=vel.device)
+    pd = _dev(data, "data", (ns, grid.nt, nrec))
+    nbytes = wave_workspace_size(grid, OP_FORWARD, src, rec)
+    work = _workspace(nbytes, vel.device)
+    g = grid.c()
+    st = _lib().wave_forward(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pd,
+                             work.data_ptr(), work.numel(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_forward")
+    return data
+
+
+def wave_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, rec_xyz, resid: torch.Tensor, src_out=None,
+                 stream=None) -> torch.Tensor:
+    """F(m)' r for every shot: [nshot][nt][nsrc]."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pr = _dev(resid, "resid", (ns, grid.nt, nrec))
+    if src_out is None:
+        src_out = torch.empty((ns, grid.nt, nsrc), dtype=torch.float32, device=vel.device)
+    po = _dev(src_out, "src_out", (ns, grid.nt, nsrc))
+    nbytes = wave_workspace_size(grid, OP_ADJOINT, src, rec)
+    work = _workspace(nbytes, vel.device)
+    g = grid.c()
+    st = _lib().wave_adjoint(ctypes.byref(g), pv, ns, nsrc, _ptr(src), nrec, _ptr(rec), pr, po, work.data_ptr(),
+                             work.numel(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_adjoint")
+    return src_out
+
+
+def wave_gradient(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, d_obs: torch.Tensor,
+                  store: int = STORE_CHECKPOINT, nsnap: int = 64, grad=None, want_dsyn: bool = False,
+                  work: torch.Tensor | None = None, stream=None):
+    """Returns (misfit, dPhi/dm [phys shape], d_syn or None)."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pw = _dev(wavelet, "wavelet", (ns, grid.nt, nsrc))
+    po = _dev(d_obs, "d_obs", (ns, grid.nt, nrec))
+    if grad is None:
+        grad = torch.empty(grid.phys_shape, dtype=torch.float32, device=vel.device)
+    pg = _dev(grad, "grad", grid.phys_shape)
+    dsyn = torch.empty((ns, grid.nt, nrec), dtype=torch.float32, device=vel.device) if want_dsyn else None
+    pds = dsyn.data_ptr() if dsyn is not None else None
+    nbytes = wave_workspace_size(grid, OP_GRADIENT, src, rec, store, nsnap)
+    if work is None or work.numel() < nbytes:
+        work = _workspace(nbytes, vel.device)
+    phi = ctypes.c_double(0.0)
+    g = grid.c()
+    st = _lib().wave_gradient(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), po, pg, pds,
+                              ctypes.byref(phi), store, nsnap, work.data_ptr(), work.numel(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_gradient")
+    return phi.value, grad, dsyn
+
+
+def wave_ricker(f0: float, dt: float, nt: int, device="cuda", out=None, stream=None) -> torch.Tensor:
+    """Ricker wavelet with peak frequency f0 delayed by 1/f0, [nt] on the GPU."""
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float32, device=device)
+    st = _lib().wave_ricker(float(f0), float(dt), int(nt), _dev(out, "out", (nt,)), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_ricker")
+    return out
+
+
+def wave_checkpoint_schedule(nt: int, nsnap: int):
+    """(forward steps, actions[n][3]) of the binomial checkpoint schedule (host only)."""
+    n = ctypes.c_int(0)
+    steps = ctypes.c_longlong(0)
+    st = _lib().wave_checkpoint_schedule(nt, nsnap, ctypes.byref(steps), None, 0, ctypes.byref(n))
+    if st:
+        raise WaveError(st, "wave_checkpoint_schedule")
+    acts = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    st = _lib().wave_checkpoint_schedule(nt, nsnap, ctypes.byref(steps), ctypes.c_void_p(acts.ctypes.data),
+                                         n.value, ctypes.byref(n))
+    if st:
+        raise WaveError(st, "wave_checkpoint_schedule")
+    return int(steps.value), acts[:n.value]
+
+
+def wave_courant_limit(ndim: int) -> float:
+    return float(_lib().wave_courant_limit(ndim))
+
+
+def wave_launch_count() -> int:
+    """Kernels libwave has launched so far in this process."""
+    return int(_lib().wave_launch_count())
+
+
+def wave_profile_start(every: int = 1) -> None:
+    """Bracket every `every`-th stencil step launch with CUDA events."""
+    st = _lib().wave_profile_start(int(every))
+    if st:
+        raise WaveError(st, "wave_profile_start")
+
+
+def wave_profile_stop():
+    """(forward ms, forward samples, adjoint ms, adjoint samples) since start."""
+    f, a = ctypes.c_double(0), ctypes.c_double(0)
+    nf, na = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    st = _lib().wave_profile_stop(ctypes.byref(f), ctypes.byref(nf), ctypes.byref(a), ctypes.byref(na))
+    if st:
+        raise WaveError(st, "wave_profile_stop")
+    return f.value, nf.value, a.value, na.value
