@@ -36,7 +36,10 @@ WORKLOAD = ("2D FWI gradient, 32 shots: 512x256 at 6.25 m, layered 1500-3500 m/s
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # the SHA-256 of the kernel source they were taken on; dropped (null) once the source changes.
-TRAFFIC = {}
+TRAFFIC = {
+    ("k_step2d<32,8,false>", "f1417c940da007d6"): 54.24e6,  # profiles/k_step2d_config2_gradient.md
+    ("k_step2d<32,8,true>", "f1417c940da007d6"): 115.45e6,
+}
 
 
 def parse():

@@ -182,3 +182,52 @@ def test_sponge_absorbs():
     d_abs = oracle.forward(oracle.Grid(2, 41, 41, h, dt, nt, 30, vref=2000.0), vel, src, q, rec)[0]
     d_ref = oracle.forward(oracle.Grid(2, 41, 41, h, dt, nt, 30, vref=0.0), vel, src, q, rec)[0]
     assert np.abs(d_abs[late]).max() < 5e-3 * np.abs(d_ref[late]).max()
+
+
+def _sponge_eta(shape, nb, h, vref):
+    """The sponge reading written out independently: eta = gamma0 (d/nb)^2 / vref^2,
+    gamma0 = 3 vref ln(1000) / (2 nb h), d = depth into the sponge in cells (max over axes)."""
+    depth = np.zeros(shape, dtype=np.int64)
+    for ax, N in enumerate(shape):
+        i = np.arange(N)
+        d1 = np.maximum(np.maximum(nb - i, i - (N - nb - 1)), 0)
+        sl = [None] * len(shape)
+        sl[ax] = slice(None)
+        depth = np.maximum(depth, d1[tuple(sl)])
+    gamma0 = 3.0 * vref * np.log(1000.0) / (2.0 * nb * h)
+    return gamma0 * (depth / nb) ** 2 / vref ** 2
+
+
+def test_energy_balance_with_damping():
+    """With damping the discrete energy drops each step by exactly
+    ||u^{n+1} - u^{n-1}||^2_E, E = diag(eta dt / 2) (inner product of the step
+    with u^{n+1} - u^{n-1}); this pins where and how eta enters the update."""
+    h = 10.0
+    vel = _two_layer(41, 35, h)
+    nb = 8
+    dt = 0.5 * oracle.courant_limit(2) * h / vel.max()
+    nt = 500
+    vref = float(vel.max())
+    g = oracle.Grid(2, 41, 35, h, dt, nt, nb, vref=vref)
+    f = 25.0
+    q = oracle.ricker(f, dt, nt)[None, :, None]
+    src = np.array([[[150.0, 60.0]]])
+    _, U = oracle.forward(g, vel, src, q, src, fields=True)
+    U = U[0]
+    m = np.pad(1.0 / vel ** 2, nb, mode="edge")
+    eta = _sponge_eta(m.shape, nb, h, vref)
+    E = eta * dt / 2
+    start = int(np.ceil(4.0 / f / dt))
+
+    def energy(n):
+        du = U[n + 1] - U[n]
+        return np.sum(m * du * du) - dt * dt * np.sum(U[n + 1] * _own_laplacian(U[n], h))
+
+    drops, preds = [], []
+    for n in range(start, nt - 1):
+        drops.append(energy(n) - energy(n - 1))
+        c = U[n + 1] - U[n - 1]
+        preds.append(-np.sum(E * c * c))
+    drops, preds = np.array(drops), np.array(preds)
+    assert np.all(preds < 0) and np.abs(preds).max() > 1e-6 * energy(start)
+    assert np.abs(drops - preds).max() <= 1e-9 * np.abs(preds).max()
