@@ -126,6 +126,27 @@ wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot
                             const float* d_obs, float* grad, float* d_syn, double* misfit, int store,
                             int nsnap, void* work, size_t work_bytes, void* stream);
 
+/* Forward modelling without a caller workspace, for callers that cannot
+ * allocate device memory when they model: e.g. a plugin whose host
+ * application has reserved all device memory up front, or a latency-critical
+ * loop that must not pay for an allocation and the synchronisation it can
+ * bring.  The paper has no counterpart; this is a deployment convenience.
+ * Same arguments, results and errors as wave_forward, minus work/work_bytes.
+ * Scratch is a file-scope device array of WAVE_STATIC_WORKSPACE_BYTES inside
+ * the library, held by every GPU that loads the library until the process
+ * exits.  Problems whose workspace (wave_workspace_size, op 0) exceeds it
+ * return WAVE_ERR_WORKSPACE before any device work.  The call allocates
+ * nothing on the device.  The first call on a device looks up the array's
+ * device address on that device (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * the array keeps the last call's contents (each call clears what must start
+ * at zero): calls that overlap on the GPU, from two streams or two host
+ * threads, race and must be serialised by the caller. */
+#define WAVE_STATIC_WORKSPACE_BYTES (32u << 20)
+wave_status_t wave_forward_static(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
+                                  const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
+                                  float* data, void* stream);
+
 /* Ricker wavelet q(t_n) = (1 - 2 a) exp(-a), a = (pi f0 (n dt - 1/f0))^2,
  * n = 0..nt-1 (the wavelet of the paper's FWI example, peak delayed by 1/f0).
  *   out dev out [nt] */

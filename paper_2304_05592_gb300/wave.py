@@ -77,6 +77,8 @@ def _lib():
         lib.wave_courant_limit.restype = ctypes.c_double
         lib.wave_status_str.argtypes = [I]
         lib.wave_status_str.restype = ctypes.c_char_p
+        lib.wave_forward_static.argtypes = [G, P, I, I, P, P, I, P, P, P]
+        lib.wave_forward_static.restype = I
         lib.wave_profile_start.argtypes = [I]
         lib.wave_profile_stop.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -182,6 +184,31 @@ def wave_forward(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, 
                              work.data_ptr(), work.numel(), _stream(stream))
     if st:
         raise WaveError(st, "wave_forward")
+    return data
+
+
+STATIC_WORKSPACE_BYTES = 32 << 20
+
+
+def wave_forward_static(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, data=None,
+                        stream=None) -> torch.Tensor:
+    """wave_forward on the library's own fixed device scratch array (no
+    workspace from the caller): for callers that cannot allocate device memory
+    when they model.  Problems needing more than 32 MiB of scratch raise
+    WAVE_ERR_WORKSPACE; calls that overlap on the GPU race (one shared array)."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pw = _dev(wavelet, "wavelet", (ns, grid.nt, nsrc))
+    if data is None:
+        data = torch.empty((ns, grid.nt, nrec), dtype=torch.float32, device=vel.device)
+    pd = _dev(data, "data", (ns, grid.nt, nrec))
+    g = grid.c()
+    st = _lib().wave_forward_static(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pd,
+                                    _stream(stream))
+    if st:
+        raise WaveError(st, "wave_forward_static")
     return data
 
 
