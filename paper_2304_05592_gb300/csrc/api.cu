@@ -4,6 +4,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
+#include <mutex>
 
 #include "internal.h"
 
@@ -29,11 +31,19 @@ struct Carver {
 
 struct DevTaps {
     TapList l;
-    int *tile_start = nullptr, *idx = nullptr, *ab = nullptr, *slot = nullptr, *pt_start = nullptr;
+    int *cell_start = nullptr, *idx = nullptr, *ab = nullptr, *slot = nullptr, *pt_start = nullptr;
     float *fac = nullptr, *gw = nullptr, *w = nullptr;
     std::vector<float> gw_host;
 };
 
+// Workspace layout.  Every field batch ([nshot][cell] floats) is one buffer of
+// a single pool with a fixed stride, so a buffer is named by its index (and one
+// TMA map covers them all):
+//   forward  : W0 W1
+//   adjoint  : A0 A1
+//   gradient : W0 W1 A0 A1 G Z S(0).cur S(0).prev ... [FP32 store rows 0..nt-1]
+// W = forward levels, A = adjoint levels, G = per-shot gradient accumulators,
+// Z = a zero batch (the state before the first step), S(k) = checkpoint slot k.
 struct Layout {
     Dims d;
     Tiling t;
@@ -45,16 +55,18 @@ struct Layout {
     double* part = nullptr;
     double* misfit = nullptr;
     float* kap = nullptr;
-    float* W[2] = {nullptr, nullptr};
-    float* A[2] = {nullptr, nullptr};
-    float* gacc = nullptr;
+    float* pool = nullptr;
+    int nbuf = 0;
+    int iW0 = -1, iA0 = -1, iG = -1, iZ = -1, iS0 = -1, iT0 = -1;
     float* slots_rec = nullptr;
     float* slots_src = nullptr;
     float* dsyn = nullptr;
-    float* snaps = nullptr;
     __nv_bfloat16* st16 = nullptr;
-    float* st32 = nullptr;
     size_t bytes = 0;
+    StepMaps maps;
+
+    size_t field() const { return (size_t)nshot * d.cell; }
+    float* buf(int i) const { return pool + (size_t)i * field(); }
 };
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
@@ -71,10 +83,10 @@ wave_status_t check_grid(const wave_grid_t* g)
     return WAVE_OK;
 }
 
-void carve_taps(Carver& c, const HostTaps& h, long long ntiles_all, DevTaps& t)
+void carve_taps(Carver& c, const HostTaps& h, long long ncells_all, DevTaps& t)
 {
     const size_t ntap = h.idx.size();
-    t.tile_start = c.take<int>(ntiles_all + 1);
+    t.cell_start = c.take<int>(ncells_all + 1);
     t.idx = c.take<int>(ntap);
     t.fac = c.take<float>(ntap);
     t.gw = c.take<float>(ntap);
@@ -82,7 +94,7 @@ void carve_taps(Carver& c, const HostTaps& h, long long ntiles_all, DevTaps& t)
     t.slot = c.take<int>(ntap);
     t.w = c.take<float>(ntap);
     t.pt_start = c.take<int>(h.pt_start.size());
-    t.l.tile_start = t.tile_start;
+    t.l.cell_start = t.cell_start;
     t.l.idx = t.idx;
     t.l.fac = t.fac;
     t.l.gw = t.gw;
@@ -113,7 +125,7 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
     if (op == 2 && (store < 0 || store > 2 || (store == WAVE_STORE_CHECKPOINT && nsnap < 1))) return WAVE_ERR_ARG;
     if ((long long)nshot * g->nt * std::max(nsrc, nrec) >= (1LL << 31)) return WAVE_ERR_ARG;
     L.d = make_dims(*g);
-    L.t = choose_tiling(L.d, nshot);
+    L.t = choose_tiling(L.d);
     L.op = op;
     L.nshot = nshot;
     L.nsrc = nsrc;
@@ -125,38 +137,41 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
     st = build_taps(d, L.t, nshot, nrec, rec_xyz, L.hr);
     if (st) return st;
 
-    const long long ntiles_all = (long long)nshot * L.t.tiles_per_shot();
-    const size_t field = (size_t)nshot * d.cell;
+    const long long ncells_all = (long long)nshot * L.t.cells_per_shot();
     const size_t nt = (size_t)d.nt;
+    if (op == 0) {
+        L.iW0 = 0;
+        L.nbuf = 2;
+    } else if (op == 1) {
+        L.iA0 = 0;
+        L.nbuf = 2;
+    } else {
+        L.iW0 = 0;
+        L.iA0 = 2;
+        L.iG = 4;
+        L.iZ = 5;
+        L.iS0 = 6;
+        L.nsnap = store == WAVE_STORE_CHECKPOINT ? std::max(0, std::min(nsnap, macro_count(d.nt))) : 0;
+        L.nbuf = 6 + 2 * L.nsnap;
+        if (store == WAVE_STORE_FP32) {
+            L.iT0 = L.nbuf;
+            L.nbuf += (int)nt;
+        }
+    }
     Carver c(base);
     L.err = c.take<int>(4);
     L.vmax = c.take<float>(1);
     L.part = c.take<double>(kNumPartials);
     L.misfit = c.take<double>(1);
     L.kap = c.take<float>(d.cell);
-    carve_taps(c, L.hs, ntiles_all, L.ts);
-    carve_taps(c, L.hr, ntiles_all, L.tr);
-    if (op == 0 || op == 2) {
-        L.W[0] = c.take<float>(field);
-        L.W[1] = c.take<float>(field);
-        L.slots_rec = c.take<float>(nt * L.hr.idx.size());
-    }
-    if (op == 1 || op == 2) {
-        L.A[0] = c.take<float>(field);
-        L.A[1] = c.take<float>(field);
-    }
+    carve_taps(c, L.hs, ncells_all, L.ts);
+    carve_taps(c, L.hr, ncells_all, L.tr);
+    L.pool = c.take<float>((size_t)L.nbuf * L.field());
+    if (op == 0 || op == 2) L.slots_rec = c.take<float>(nt * L.hr.idx.size());
     if (op == 1) L.slots_src = c.take<float>(nt * L.hs.idx.size());
     if (op == 2) {
-        L.gacc = c.take<float>(field);
         L.dsyn = c.take<float>((size_t)nshot * nt * nrec);
-        if (store == WAVE_STORE_CHECKPOINT) {
-            L.nsnap = std::max(0, std::min(nsnap, macro_count(d.nt)));
-            L.snaps = c.take<float>((size_t)L.nsnap * 2 * field);
-        } else if (store == WAVE_STORE_BF16) {
-            L.st16 = c.take<__nv_bfloat16>(nt * field);
-        } else {
-            L.st32 = c.take<float>(nt * field);
-        }
+        if (store == WAVE_STORE_BF16) L.st16 = c.take<__nv_bfloat16>(nt * L.field());
     }
     L.bytes = c.off;
     // Gather weights: receivers sample with w; the source-side adjoint
@@ -168,18 +183,81 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
     return WAVE_OK;
 }
 
-#define CK(x)                                 \
-    do {                                      \
-        if ((x) != cudaSuccess) {             \
-            (void)cudaGetLastError();         \
-            return WAVE_ERR_CUDA;             \
-        }                                     \
+#define CK(x)                         \
+    do {                              \
+        if ((x) != cudaSuccess) {     \
+            (void)cudaGetLastError(); \
+            return WAVE_ERR_CUDA;     \
+        }                             \
     } while (0)
+
+// --- TMA descriptors -------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+bool encode(CUtensorMap* m, CUtensorMapDataType type, int rank, void* ptr, const cuuint64_t* dims,
+            const cuuint64_t* strides, const cuuint32_t* box)
+{
+    EncodeTiledFn fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return fn(m, type, (cuuint32_t)rank, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Maps over the field pool, the model and the BF16 store (the 2D kernels use them).
+wave_status_t make_maps(Layout& L)
+{
+    memset(&L.maps, 0, sizeof(L.maps));
+    if (L.d.ndim != 2) return WAVE_OK;
+    const Dims& d = L.d;
+    const cuuint64_t fdims[4] = {(cuuint64_t)d.Nx, (cuuint64_t)d.Nz, (cuuint64_t)L.nshot, (cuuint64_t)L.nbuf};
+    const cuuint64_t fstr[3] = {(cuuint64_t)d.P * 4, (cuuint64_t)d.cell * 4, (cuuint64_t)L.field() * 4};
+    const cuuint64_t kdims[2] = {(cuuint64_t)d.Nx, (cuuint64_t)d.Nz};
+    const cuuint64_t kstr[1] = {(cuuint64_t)d.P * 4};
+    const cuuint32_t tzf = (cuuint32_t)variant_info(0, L.t.vf).TZ, tza = (cuuint32_t)variant_info(1, L.t.va).TZ;
+    const cuuint32_t hb_f[4] = {kTX + 8, tzf + 8, 1, 1}, tb_f[4] = {kTX, tzf, 1, 1};
+    const cuuint32_t hb_a[4] = {kTX + 8, tza + 8, 1, 1}, tb_a[4] = {kTX, tza, 1, 1};
+    bool ok = encode(&L.maps.halo_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.pool, fdims, fstr, hb_f) &&
+              encode(&L.maps.tile_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.pool, fdims, fstr, tb_f) &&
+              encode(&L.maps.halo_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.pool, fdims, fstr, hb_a) &&
+              encode(&L.maps.tile_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.pool, fdims, fstr, tb_a) &&
+              encode(&L.maps.kap_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, L.kap, kdims, kstr, tb_f) &&
+              encode(&L.maps.kap_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, L.kap, kdims, kstr, tb_a);
+    if (ok && L.st16) {
+        const cuuint64_t sdims[4] = {(cuuint64_t)d.Nx, (cuuint64_t)d.Nz, (cuuint64_t)L.nshot, (cuuint64_t)d.nt};
+        const cuuint64_t sstr[3] = {(cuuint64_t)d.P * 2, (cuuint64_t)d.cell * 2, (cuuint64_t)L.field() * 2};
+        ok = encode(&L.maps.tile16_a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, L.st16, sdims, sstr, tb_a);
+    }
+    return ok ? WAVE_OK : WAVE_ERR_CUDA;
+}
+
+// --- set-up ----------------------------------------------------------------
 
 wave_status_t upload_taps(const HostTaps& h, DevTaps& t, cudaStream_t s)
 {
     const size_t ntap = h.idx.size();
-    CK(cudaMemcpyAsync(t.tile_start, h.tile_start.data(), h.tile_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.cell_start, h.cell_start.data(), h.cell_start.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       s));
     CK(cudaMemcpyAsync(t.pt_start, h.pt_start.data(), h.pt_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     if (ntap) {
         CK(cudaMemcpyAsync(t.idx, h.idx.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -208,7 +286,8 @@ float sponge_coefficient(const Dims& d)
     return (float)(3.0 * log(1000.0) * d.h / (4.0 * d.dt * d.vref * nb * nb * nb));
 }
 
-// Uploads tables, prepares the model, validates it and fills the injection factors.
+// Uploads tables, prepares the model, validates it, fills the injection
+// factors and encodes the TMA maps.
 wave_status_t setup(Layout& L, const float* vel, cudaStream_t s)
 {
     wave_status_t st = upload_taps(L.hs, L.ts, s);
@@ -233,7 +312,7 @@ wave_status_t setup(Layout& L, const float* vel, cudaStream_t s)
     // Adjoint receiver injection adds w r / (m + e) = kap (h/dt)^2 w r / (1 + eps).
     launch_tapfac(L.d, L.tr.l, L.kap, (float)(h * h / (dt * dt)), ceps, s);
     CK(cudaGetLastError());
-    return WAVE_OK;
+    return make_maps(L);
 }
 
 StepArgs base_args(const Layout& L)
@@ -251,22 +330,29 @@ StepArgs base_args(const Layout& L)
     a.nx = d.nx;
     a.ny = d.ny;
     a.nz = d.nz;
+    a.nshot = L.nshot;
     a.ceps = sponge_coefficient(d);
-    a.ntx = L.t.ntx;
-    a.nty = L.t.nty;
-    a.ntz = L.t.ntz;
+    a.ncx = L.t.ncx;
+    a.ncy = L.t.ncy;
+    a.ncz = L.t.ncz;
+    a.TZc = L.t.TZc;
     a.err = L.err;
+    a.u_buf = a.prev_buf = a.uf_buf = a.g_buf = a.uf16_row = -1;
     return a;
 }
 
-// Forward step n: u^{n+1} into `unew` (which holds u^{n-1}), injecting q^n;
-// optionally records d^{n+1} and stores u^{n+1}.
-void fwd_step(const Layout& L, const float* u, float* unew, int n, const float* wavelet, bool record,
+// Forward step n: reads u^n (buffer cur) and u^{n-1} (buffer prev), writes
+// u^{n+1} into buffer out (which may be prev), injecting q^n; optionally
+// records d^{n+1} and stores u^{n+1} (BF16 row or FP32 buffer).
+void fwd_step(const Layout& L, int cur, int prev, int out, int n, const float* wavelet, bool record,
               __nv_bfloat16* st16, float* st32, cudaStream_t s)
 {
     StepArgs a = base_args(L);
-    a.u = u;
-    a.unew = unew;
+    a.u = L.buf(cur);
+    a.uprev = L.buf(prev);
+    a.unew = L.buf(out);
+    a.u_buf = cur;
+    a.prev_buf = prev;
     if (L.nsrc > 0 && L.ts.l.ntap > 0) {
         a.inj = L.ts.l;
         a.amp_a = wavelet;
@@ -279,18 +365,23 @@ void fwd_step(const Layout& L, const float* u, float* unew, int n, const float* 
     }
     a.st16 = st16;
     a.st32 = st32;
-    launch_step(L.t, L.d.ndim, false, L.nshot, a, s);
+    launch_step(L.t, L.d.ndim, false, a, &L.maps, s);
 }
 
-// Adjoint step k: mu^k into `mu0` (which holds mu^{k+2}), injecting
-// amp_a - amp_b at time k at the receivers; optionally gathers the source-side
-// adjoint (F' r)^{k-1} and accumulates the imaging condition with u^k.
-void adj_step(const Layout& L, const float* mu1, float* mu0, int k, const float* amp_a, const float* amp_b,
-              bool gather_src, const float* uf32, const __nv_bfloat16* uf16, float* gacc, cudaStream_t s)
+// Adjoint step k: reads mu^{k+1} (buffer cur) and mu^{k+2} (buffer prev),
+// writes mu^k over mu^{k+2}, injecting amp_a - amp_b at time k at the
+// receivers; optionally gathers the source-side adjoint (F' r)^{k-1}; with a
+// forward field (buffer uf, or BF16 row uf16_row) accumulates the imaging
+// condition into the gradient buffer.
+void adj_step(const Layout& L, int cur, int prev, int k, const float* amp_a, const float* amp_b, bool gather_src,
+              int uf, int uf16_row, cudaStream_t s)
 {
     StepArgs a = base_args(L);
-    a.u = mu1;
-    a.unew = mu0;
+    a.u = L.buf(cur);
+    a.uprev = L.buf(prev);
+    a.unew = L.buf(prev);
+    a.u_buf = cur;
+    a.prev_buf = prev;
     if (L.nrec > 0 && L.tr.l.ntap > 0) {
         a.inj = L.tr.l;
         a.amp_a = amp_a;
@@ -302,10 +393,18 @@ void adj_step(const Layout& L, const float* mu1, float* mu0, int k, const float*
         a.slots = L.slots_src;
         a.slot_row = k - 1;
     }
-    a.uf32 = uf32;
-    a.uf16 = uf16;
-    a.gacc = gacc;
-    launch_step(L.t, L.d.ndim, true, L.nshot, a, s);
+    if (uf >= 0 || uf16_row >= 0) {
+        a.gacc = L.buf(L.iG);
+        a.g_buf = L.iG;
+        if (uf >= 0) {
+            a.uf32 = L.buf(uf);
+            a.uf_buf = uf;
+        } else {
+            a.uf16 = L.st16 + (size_t)uf16_row * L.field();
+            a.uf16_row = uf16_row;
+        }
+    }
+    launch_step(L.t, L.d.ndim, true, a, &L.maps, s);
 }
 
 wave_status_t finish(const Layout& L, cudaStream_t s)
@@ -324,6 +423,81 @@ wave_status_t check_work(const Layout& L, void* work, size_t work_bytes)
 {
     if (L.bytes > 0 && (!work || work_bytes < L.bytes)) return WAVE_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(work) % 256) return WAVE_ERR_WORKSPACE;
+    return WAVE_OK;
+}
+
+// Runs the binomial checkpoint schedule without copying states: a restore
+// only renames which buffers hold (u^j, u^{j-1}), the last two steps of an
+// advance that ends in a save write straight into the slot, and a step that
+// starts from a slot writes out of place into W0/W1.
+wave_status_t run_checkpointed(Layout& L, const float* wavelet, const float* d_obs,
+                               const std::function<void()>& finalize_data, cudaStream_t s)
+{
+    const Dims& d = L.d;
+    const Schedule sch = make_schedule(d.nt, L.nsnap);
+    const int W0 = L.iW0, W1 = L.iW0 + 1, Z = L.iZ, A0 = L.iA0;
+    auto slot_cur = [&](int k) { return L.iS0 + 2 * k; };
+    auto slot_prev = [&](int k) { return L.iS0 + 2 * k + 1; };
+    int cur = Z, prev = Z, state = 0, recorded = 0, acur = 0;
+    const size_t fb = L.field() * sizeof(float);
+    for (size_t ai = 0; ai < sch.actions.size(); ++ai) {
+        const Action& act = sch.actions[ai];
+        switch (act.kind) {
+        case kAdvance: {
+            const int j0 = sch.state_of(act.a), j1 = sch.state_of(act.b);
+            if (j0 != state) return WAVE_ERR_ARG;  // inconsistent schedule (not reachable)
+            const bool to_slot = ai + 1 < sch.actions.size() && sch.actions[ai + 1].kind == kSave;
+            const int slot = to_slot ? sch.actions[ai + 1].a : -1;
+            for (int n = j0; n < j1; ++n) {
+                int out;
+                if (to_slot && n == j1 - 1) out = slot_cur(slot);
+                else if (to_slot && n == j1 - 2) out = slot_prev(slot);
+                else if (prev == W0 || prev == W1) out = prev;
+                else out = cur == W0 ? W1 : W0;
+                const bool rec = n >= recorded;
+                fwd_step(L, cur, prev, out, n, wavelet, rec, nullptr, nullptr, s);
+                if (rec) recorded = n + 1;
+                prev = cur;
+                cur = out;
+            }
+            state = j1;
+            break;
+        }
+        case kSave: {
+            const int k = act.a;
+            if (cur != slot_cur(k)) CK(cudaMemcpyAsync(L.buf(slot_cur(k)), L.buf(cur), fb, cudaMemcpyDeviceToDevice, s));
+            if (prev != slot_prev(k))
+                CK(cudaMemcpyAsync(L.buf(slot_prev(k)), L.buf(prev), fb, cudaMemcpyDeviceToDevice, s));
+            cur = slot_cur(k);
+            prev = slot_prev(k);
+            break;
+        }
+        case kRestore:
+            if (act.a < 0) {
+                cur = prev = Z;
+            } else {
+                cur = slot_cur(act.a);
+                prev = slot_prev(act.a);
+            }
+            state = sch.state_of(act.b);
+            break;
+        case kFinalize:
+            if (recorded != sch.K) return WAVE_ERR_ARG;  // not reachable
+            finalize_data();
+            break;
+        case kAdjointPair: {
+            const int j = sch.state_of(act.a);
+            if (j != state) return WAVE_ERR_ARG;  // not reachable
+            adj_step(L, A0 + acur, A0 + 1 - acur, j, L.dsyn, d_obs, false, cur, -1, s);
+            acur ^= 1;
+            if (j - 1 >= 1) {
+                adj_step(L, A0 + acur, A0 + 1 - acur, j - 1, L.dsyn, d_obs, false, prev, -1, s);
+                acur ^= 1;
+            }
+            break;
+        }
+        }
+    }
     return WAVE_OK;
 }
 
@@ -371,14 +545,13 @@ wave_status_t wave_forward(const wave_grid_t* grid, const float* vel, int nshot,
     if (!vel || (nsrc && !wavelet) || (nrec && !data)) return WAVE_ERR_ARG;
     if ((st = check_work(L, work, work_bytes))) return st;
     if ((st = setup(L, vel, s))) return st;
-    const size_t fb = (size_t)nshot * L.d.cell * sizeof(float);
-    CK(cudaMemsetAsync(L.W[0], 0, fb, s));
-    CK(cudaMemsetAsync(L.W[1], 0, fb, s));
+    const size_t fb = L.field() * sizeof(float);
+    CK(cudaMemsetAsync(L.buf(0), 0, 2 * fb, s));
     const size_t nrow = L.hr.idx.size();
     if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
     int cur = 0;
     for (int n = 0; n + 1 < L.d.nt; ++n) {
-        fwd_step(L, L.W[cur], L.W[1 - cur], n, wavelet, true, nullptr, nullptr, s);
+        fwd_step(L, cur, 1 - cur, 1 - cur, n, wavelet, true, nullptr, nullptr, s);
         cur ^= 1;
     }
     if (nrec) {
@@ -400,14 +573,13 @@ wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot,
     if (!vel || (nrec && !resid) || (nsrc && !src_out)) return WAVE_ERR_ARG;
     if ((st = check_work(L, work, work_bytes))) return st;
     if ((st = setup(L, vel, s))) return st;
-    const size_t fb = (size_t)nshot * L.d.cell * sizeof(float);
-    CK(cudaMemsetAsync(L.A[0], 0, fb, s));
-    CK(cudaMemsetAsync(L.A[1], 0, fb, s));
+    const size_t fb = L.field() * sizeof(float);
+    CK(cudaMemsetAsync(L.buf(0), 0, 2 * fb, s));
     const size_t nrow = L.hs.idx.size();
     if (nrow) CK(cudaMemsetAsync(L.slots_src + (size_t)(L.d.nt - 1) * nrow, 0, nrow * sizeof(float), s));
     int cur = 0;
     for (int k = L.d.nt - 1; k >= 1; --k) {
-        adj_step(L, L.A[cur], L.A[1 - cur], k, resid, nullptr, true, nullptr, nullptr, nullptr, s);
+        adj_step(L, cur, 1 - cur, k, resid, nullptr, true, -1, -1, s);
         cur ^= 1;
     }
     if (nsrc) {
@@ -436,13 +608,10 @@ wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot
         return WAVE_OK;
     }
     if ((st = setup(L, vel, s))) return st;
-    const size_t field = (size_t)nshot * d.cell;
+    const size_t field = L.field();
     const size_t fb = field * sizeof(float);
-    for (int i = 0; i < 2; ++i) {
-        CK(cudaMemsetAsync(L.W[i], 0, fb, s));
-        CK(cudaMemsetAsync(L.A[i], 0, fb, s));
-    }
-    CK(cudaMemsetAsync(L.gacc, 0, fb, s));
+    // W0 W1 A0 A1 G Z are contiguous: clear them in one go.
+    CK(cudaMemsetAsync(L.buf(0), 0, 6 * fb, s));
     const size_t nrow = L.hr.idx.size();
     if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
     const long long ndata = (long long)nshot * d.nt * nrec;
@@ -457,82 +626,32 @@ wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot
         }
     };
 
+    const int W0 = L.iW0, A0 = L.iA0;
     if (store != WAVE_STORE_CHECKPOINT) {
         if (L.st16) CK(cudaMemsetAsync(L.st16, 0, field * sizeof(__nv_bfloat16), s));
-        if (L.st32) CK(cudaMemsetAsync(L.st32, 0, fb, s));
+        if (L.iT0 >= 0) CK(cudaMemsetAsync(L.buf(L.iT0), 0, fb, s));
         int cur = 0;
         for (int n = 0; n < K; ++n) {
             __nv_bfloat16* r16 = L.st16 ? L.st16 + (size_t)(n + 1) * field : nullptr;
-            float* r32 = L.st32 ? L.st32 + (size_t)(n + 1) * field : nullptr;
-            fwd_step(L, L.W[cur], L.W[1 - cur], n, wavelet, true, r16, r32, s);
+            float* r32 = L.iT0 >= 0 ? L.buf(L.iT0 + n + 1) : nullptr;
+            fwd_step(L, W0 + cur, W0 + 1 - cur, W0 + 1 - cur, n, wavelet, true, r16, r32, s);
             cur ^= 1;
         }
         finalize_data();
         int acur = 0;
         for (int k = K; k >= 1; --k) {
-            const __nv_bfloat16* u16 = L.st16 ? L.st16 + (size_t)k * field : nullptr;
-            const float* u32 = L.st32 ? L.st32 + (size_t)k * field : nullptr;
-            adj_step(L, L.A[acur], L.A[1 - acur], k, L.dsyn, d_obs, false, u32, u16, L.gacc, s);
+            if (L.st16) adj_step(L, A0 + acur, A0 + 1 - acur, k, L.dsyn, d_obs, false, -1, k, s);
+            else adj_step(L, A0 + acur, A0 + 1 - acur, k, L.dsyn, d_obs, false, L.iT0 + k, -1, s);
             acur ^= 1;
         }
     } else if (K < 1) {
         finalize_data();
     } else {
-        const Schedule sch = make_schedule(d.nt, L.nsnap);
-        int wcur = 0, wstate = 0, recorded = 0, acur = 0;
-        for (const Action& act : sch.actions) {
-            switch (act.kind) {
-            case kAdvance: {
-                const int j0 = sch.state_of(act.a), j1 = sch.state_of(act.b);
-                if (j0 != wstate) return WAVE_ERR_ARG;  // schedule inconsistency (not reachable)
-                for (int n = j0; n < j1; ++n) {
-                    const bool rec = n >= recorded;
-                    fwd_step(L, L.W[wcur], L.W[1 - wcur], n, wavelet, rec, nullptr, nullptr, s);
-                    if (rec) recorded = n + 1;
-                    wcur ^= 1;
-                }
-                wstate = j1;
-                break;
-            }
-            case kSave: {
-                float* slot = L.snaps + (size_t)act.a * 2 * field;
-                CK(cudaMemcpyAsync(slot, L.W[wcur], fb, cudaMemcpyDeviceToDevice, s));
-                CK(cudaMemcpyAsync(slot + field, L.W[1 - wcur], fb, cudaMemcpyDeviceToDevice, s));
-                break;
-            }
-            case kRestore: {
-                if (act.a < 0) {
-                    CK(cudaMemsetAsync(L.W[0], 0, fb, s));
-                    CK(cudaMemsetAsync(L.W[1], 0, fb, s));
-                } else {
-                    const float* slot = L.snaps + (size_t)act.a * 2 * field;
-                    CK(cudaMemcpyAsync(L.W[0], slot, fb, cudaMemcpyDeviceToDevice, s));
-                    CK(cudaMemcpyAsync(L.W[1], slot + field, fb, cudaMemcpyDeviceToDevice, s));
-                }
-                wcur = 0;
-                wstate = sch.state_of(act.b);
-                break;
-            }
-            case kFinalize:
-                if (recorded != K) return WAVE_ERR_ARG;  // not reachable
-                finalize_data();
-                break;
-            case kAdjointPair: {
-                const int j = sch.state_of(act.a);
-                if (j != wstate) return WAVE_ERR_ARG;  // not reachable
-                adj_step(L, L.A[acur], L.A[1 - acur], j, L.dsyn, d_obs, false, L.W[wcur], nullptr, L.gacc, s);
-                acur ^= 1;
-                if (j - 1 >= 1) {
-                    adj_step(L, L.A[acur], L.A[1 - acur], j - 1, L.dsyn, d_obs, false, L.W[1 - wcur], nullptr,
-                             L.gacc, s);
-                    acur ^= 1;
-                }
-                break;
-            }
-            }
-        }
+        st = run_checkpointed(L, wavelet, d_obs, finalize_data, s);
+        if (st) return st;
     }
-    launch_grad_reduce(d, L.gacc, nshot, grad, s);
+    // A0 and A1 (contiguous) are free now: scratch for the reduction.
+    launch_grad_reduce(d, L.buf(L.iG), nshot, L.buf(A0), grad, s);
     launch_nan_scan(grad, d.phys, L.err, s);
     if (d_syn && ndata) CK(cudaMemcpyAsync(d_syn, L.dsyn, ndata * sizeof(float), cudaMemcpyDeviceToDevice, s));
     double hm = 0.0;
@@ -551,6 +670,13 @@ wave_status_t wave_ricker(float f0, float dt, int nt, float* out, void* stream)
     CK(cudaGetLastError());
     return WAVE_OK;
 }
+
+wave_status_t wave_set_variant(int which, int variant)
+{
+    return select_variant(which, variant) == 0 ? WAVE_OK : WAVE_ERR_ARG;
+}
+
+int wave_variant_count(int which) { return variant_count(which); }
 
 wave_status_t wave_checkpoint_schedule(int nt, int nsnap, long long* fwd_steps, int* actions, int capacity,
                                        int* nactions)

@@ -1,6 +1,7 @@
 // internal.h -- types shared by the libwave translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -21,9 +22,8 @@ constexpr float kC4 = -1.0f / 560.0f;
 
 // Device error word bits.
 enum : int {
-    kErrNonFinite = 1,  // velocity not finite/positive or NaN in a field
-    kErrTimeout = 2,    // a bounded wait ran out
-    kErrIndex = 4       // an internal index check failed (a tap outside its tile)
+    kErrNonFinite = 1,  // velocity not finite/positive or NaN in a result
+    kErrTimeout = 2     // a bounded wait ran out
 };
 
 // Padded geometry of one shot's field.  Fields are stored [Nz][Ny][P] floats
@@ -39,20 +39,21 @@ struct Dims {
 
 Dims make_dims(const wave_grid_t& g);
 
-// Tiling of the padded grid used by the stencil kernels.  A tile is the set of
-// points whose update one CTA writes: TX x TY x TZ (TY = 1 in 2D).
+// Partition of the padded grid.  Interpolation taps are grouped per "cell"
+// (TX x TY x TZc points) in the order (shot, cx, cy, cz) with cz fastest, so
+// that a kernel tile covering k consecutive cells along z owns one contiguous
+// range of taps.
 struct Tiling {
-    int TX, TY, TZ;
-    int ntx, nty, ntz;  // tiles per shot along each axis
-    int kind;           // kernel variant id (see kernels)
-    long long tiles_per_shot() const { return (long long)ntx * nty * ntz; }
+    int TX, TY, TZc;
+    int ncx, ncy, ncz;
+    int vf, va;  // 2D kernel variants for the forward / adjoint steps
+    long long cells_per_shot() const { return (long long)ncx * ncy * ncz; }
 };
 
 // One list of interpolation taps (sources or receivers) in device memory,
-// grouped per (shot, tile) so that the CTA updating a tile handles exactly the
-// taps that fall in it.
+// grouped per (shot, cell).
 struct TapList {
-    const int* tile_start = nullptr;  // [nshot * tiles_per_shot + 1]
+    const int* cell_start = nullptr;  // [nshot * cells_per_shot + 1]
     const int* idx = nullptr;         // flat index inside the shot's field
     const float* fac = nullptr;       // injection factor (filled on device)
     const float* gw = nullptr;        // gather weight
@@ -64,28 +65,38 @@ struct TapList {
     const int* pt_start = nullptr;    // [nshot * npts + 1] taps of each point (point order)
 };
 
-// Host-side tap tables before upload.
 struct HostTaps {
-    std::vector<int> tile_start, idx, ab, slot, pt_start;
+    std::vector<int> cell_start, idx, ab, slot, pt_start;
     std::vector<float> w;
     int npts = 0;
 };
 
-// Builds taps for nshot * npts points; returns WAVE_ERR_GEOMETRY for a point
-// outside the physical grid.
-wave_status_t build_taps(const Dims& d, const Tiling& t, int nshot, int npts, const float* xyz,
-                         HostTaps& out);
+// Builds taps for nshot * npts points; WAVE_ERR_GEOMETRY for a point outside
+// the physical grid.
+wave_status_t build_taps(const Dims& d, const Tiling& t, int nshot, int npts, const float* xyz, HostTaps& out);
+
+// TMA descriptors.  Every field batch ([nshot][Nz][P]) of a call lives in one
+// pool of equally sized buffers, so one 4D map addresses any of them through a
+// buffer-index coordinate.  halo: box of the stencil input with its 4-point
+// halo; tile: box of a pointwise input; kap: the model; tile16: the BF16 store.
+// _f / _a: boxes for the forward / adjoint tile heights.
+struct StepMaps {
+    CUtensorMap halo_f, tile_f, kap_f, halo_a, tile_a, kap_a, tile16_a;
+};
 
 // Arguments of one time step of the stencil kernels.
 struct StepArgs {
-    const float* u;      // [nshot][cell] field at the current time level
-    float* unew;         // [nshot][cell] in: previous level, out: next level
+    const float* u;      // [nshot][cell] field at the current level
+    const float* uprev;  // [nshot][cell] previous level
+    float* unew;         // [nshot][cell] next level (may alias uprev)
     const float* kap;    // [cell] (v dt / h)^2
     int Nx, Ny, Nz, P;
     long long cell;
     int nb, nx, ny, nz;
+    int nshot;
     float ceps;          // eps = kap * ceps * depth^2 is eta dt v^2 / 2
-    int ntx, nty, ntz;
+    int ncx, ncy, ncz;   // tap cells per shot
+    int TZc;             // tap cell height
     // injection into unew (forward: sources with q^n; adjoint: receivers with r^k)
     TapList inj;
     const float* amp_a;  // amplitude array [nshot][nt][npts]
@@ -98,24 +109,40 @@ struct StepArgs {
     // forward: optional copy of unew to a store row
     __nv_bfloat16* st16;
     float* st32;
-    // adjoint: forward field u^k for the imaging condition, per-shot accumulators
+    // adjoint: forward field u^k for the imaging condition, gradient accumulators
     const __nv_bfloat16* uf16;
     const float* uf32;
     float* gacc;         // [nshot][cell]
     int* err;
+    // pool indices of the same buffers for the TMA kernels (-1: none)
+    int u_buf, prev_buf, uf_buf, g_buf, uf16_row;
 };
 
 // Kernel launchers (kernels.cu).
-void launch_step(const Tiling& t, int ndim, bool adjoint, int nshot, const StepArgs& a, cudaStream_t s);
+void launch_step(const Tiling& t, int ndim, bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s);
 void launch_prep(const Dims& d, const float* vel, float* kap, float* vmax, int* err, cudaStream_t s);
 void launch_tapfac(const Dims& d, const TapList& l, const float* kap, float scale_inj, float ceps,
                    cudaStream_t s);
 void launch_finalize(const TapList& l, const float* slots, int nshot, int nt, float* out, cudaStream_t s);
 void launch_misfit(const float* a, const float* b, long long n, double* partial, int npart, double* out,
                    cudaStream_t s);
-void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* grad, cudaStream_t s);
+void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp, float* grad, cudaStream_t s);
 void launch_ricker(float f0, float dt, int nt, float* out, cudaStream_t s);
 void launch_nan_scan(const float* a, long long n, int* err, cudaStream_t s);
+
+// Tile geometry of the 2D steps (kernels.cu).
+constexpr int kTX = 128;          // x points per tile (32 lanes x 4)
+constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile height
+
+// 2D kernel variants: direct loads (kind 0) or the persistent TMA pipeline
+// (kind 1) with tile height TZ, R rows per warp and NST stages.
+struct Variant2D {
+    int kind, TZ, R, NST;
+};
+int variant_count(int which);             // which: 0 forward, 1 adjoint
+Variant2D variant_info(int which, int v);
+int current_variant(int which);           // the selected or default variant
+int select_variant(int which, int v);     // v = -1 restores the default; 0 on success
 
 // Launch accounting and sampled per-launch timing of the stencil kernels
 // (profile.cu).  Every launcher above calls count_launch(); launch_step wraps
@@ -125,7 +152,7 @@ bool profile_sample(bool adjoint, cudaStream_t s, cudaEvent_t* stop);
 void profile_close(cudaEvent_t stop, cudaStream_t s);
 
 // Tiling choice (plan.cu).
-Tiling choose_tiling(const Dims& d, int nshot);
+Tiling choose_tiling(const Dims& d);
 
 // Binomial checkpoint schedule (plan.cu).
 enum ActionKind { kAdvance = 0, kSave = 1, kRestore = 2, kAdjointPair = 3, kFinalize = 4 };

@@ -2,10 +2,15 @@
 // small kernels around it (model preparation, tap factors, gathers, misfit,
 // shot reduction of the gradient, Ricker wavelet).
 //
-// Every kernel here is HBM/L2-bandwidth bound: FP32 arithmetic on CUDA cores,
-// 128-bit loads and stores, halo tiles in shared memory.  Tensor cores play no
-// part (the stencil is not a dense contraction).
+// All of it is memory bound: FP32 arithmetic on CUDA cores, 128-bit accesses,
+// halo tiles in shared memory.  Tensor cores play no part (the stencil is not
+// a dense contraction).  The 2D step comes in two families selected per call:
+// a direct-load kernel with a shared-memory halo tile, and a persistent kernel
+// that streams tiles through shared memory with TMA (cp.async.bulk.tensor) and
+// mbarriers, keeping one to three tiles of loads in flight per SM.
 #include <math.h>
+
+#include <algorithm>
 
 #include "internal.h"
 
@@ -26,6 +31,7 @@ __device__ __forceinline__ float leap(float c, float um, float lap, float kap, f
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ float f4(const float4& v, int i)
 {
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -41,9 +47,8 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* p, const float* o)
     *reinterpret_cast<uint2*>(p) = v;
 }
 
-__device__ __forceinline__ void load_bf16x4(const __nv_bfloat16* p, float* o)
+__device__ __forceinline__ void unpack_bf16x4(uint2 v, float* o)
 {
-    uint2 v = *reinterpret_cast<const uint2*>(p);
     __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&v.x);
     __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&v.y);
     float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
@@ -53,19 +58,125 @@ __device__ __forceinline__ void load_bf16x4(const __nv_bfloat16* p, float* o)
     o[3] = b.y;
 }
 
-// Writes the four updated points of one thread (x .. x+3 of one row) and, in
-// the forward pass, their stored copy; in the adjoint pass accumulates the
-// imaging condition g -= u^k (mu^k - 2 mu^{k+1} + mu^{k+2}).
+// ---------------------------------------------------------------------------
+// mbarrier and TMA (inline PTX, sm_90+ forms that sm_103a keeps).
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (TMA) writes to it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier phase: false after ~4M polls (seconds), so a copy
+// that never lands turns into an error status instead of a hung GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(c3)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Sparse part of a step, run by the CTA that owns a tile after its points are
+// written: injection into unew, then gathers of unew into slots.  [ib, ie) and [gb, ge) are the
+// tile's ranges in the injection and gather tap lists.
 template <bool ADJ>
-__device__ __forceinline__ void finish4(const StepArgs& a, long long so, long long off, int nvalid,
-                                        const float* out, const float* cen, const float* um)
+__device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, int gb, int ge, long long so, int tid,
+                                             int nthr)
 {
     float* un = a.unew + so;
-    if (nvalid == 4) {
-        *reinterpret_cast<float4*>(un + off) = make_float4(out[0], out[1], out[2], out[3]);
-    } else {
-        for (int i = 0; i < nvalid; ++i) un[off + i] = out[i];
+    if (a.inj.cell_start) {
+        // Taps are sorted by grid point inside each cell: the thread holding the
+        // first tap of a point sums that point's taps in a fixed order and owns
+        // the update, so no atomics are needed and results are repeatable.
+        for (int j = ib + tid; j < ie; j += nthr) {
+            const int i = a.inj.idx[j];
+            if (j > ib && a.inj.idx[j - 1] == i) continue;
+            float add = 0.0f;
+            for (int jj = j; jj < ie && a.inj.idx[jj] == i; ++jj) {
+                const long long ai = (long long)a.inj.ab[jj] + (long long)a.amp_row * a.inj.npts;
+                float amp = a.amp_a[ai];
+                if (a.amp_b) amp -= a.amp_b[ai];
+                add = fmaf(a.inj.fac[jj], amp, add);
+            }
+            const float v = un[i] + add;
+            un[i] = v;
+            if (!ADJ) {
+                // the stored copy of the new level must include the injection
+                if (a.st16) a.st16[so + i] = __float2bfloat16_rn(v);
+                if (a.st32) a.st32[so + i] = v;
+            } else if (a.gacc) {
+                const float uf = a.uf16 ? __bfloat162float(a.uf16[so + i]) : a.uf32[so + i];
+                a.gacc[so + i] -= uf * add;
+            }
+        }
     }
+    if (a.gat.cell_start) {
+        __syncthreads();
+        float* row = a.slots + (long long)a.slot_row * a.gat.ntap;
+        for (int j = gb + tid; j < ge; j += nthr) row[a.gat.slot[j]] = a.gat.gw[j] * un[a.gat.idx[j]];
+    }
+}
+
+// Writes one thread's four updated points (zeros past Nx) and, in the forward
+// pass, their stored copies; in the adjoint pass adds the imaging term
+// g -= u^k (mu^k - 2 mu^{k+1} + mu^{k+2}) to the loaded accumulator values.
+template <bool ADJ>
+__device__ __forceinline__ void write4(const StepArgs& a, long long so, long long off, int nvalid, const float* out,
+                                       const float* cen, const float* um, bool imaging, const float* uf, float4 gv)
+{
+    float* un = a.unew + so;
+    // Always a full float4: points past Nx are the zero exterior that the next
+    // step's halo loads read, so every output buffer keeps them zero.
+    *reinterpret_cast<float4*>(un + off) = make_float4(out[0], nvalid > 1 ? out[1] : 0.0f,
+                                                       nvalid > 2 ? out[2] : 0.0f, nvalid > 3 ? out[3] : 0.0f);
     if (!ADJ) {
         if (a.st16) {
             if (nvalid == 4) {
@@ -81,157 +192,320 @@ __device__ __forceinline__ void finish4(const StepArgs& a, long long so, long lo
                 for (int i = 0; i < nvalid; ++i) a.st32[so + off + i] = out[i];
             }
         }
-    } else if (a.gacc) {
-        float uf[4];
-        if (a.uf16) {
-            if (nvalid == 4) {
-                load_bf16x4(a.uf16 + so + off, uf);
-            } else {
-                for (int i = 0; i < nvalid; ++i) uf[i] = __bfloat162float(a.uf16[so + off + i]);
-            }
-        } else {
-            if (nvalid == 4) {
-                float4 v = ld4(a.uf32 + so + off);
-                uf[0] = v.x;
-                uf[1] = v.y;
-                uf[2] = v.z;
-                uf[3] = v.w;
-            } else {
-                for (int i = 0; i < nvalid; ++i) uf[i] = a.uf32[so + off + i];
-            }
-        }
-        float* g = a.gacc + so + off;
+    } else if (imaging) {
+        float g[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g[i] -= uf[i] * (out[i] - 2.0f * cen[i] + um[i]);
+        float* gp = a.gacc + so + off;
         if (nvalid == 4) {
-            float4 gv = *reinterpret_cast<float4*>(g);
-            gv.x -= uf[0] * (out[0] - 2.0f * cen[0] + um[0]);
-            gv.y -= uf[1] * (out[1] - 2.0f * cen[1] + um[1]);
-            gv.z -= uf[2] * (out[2] - 2.0f * cen[2] + um[2]);
-            gv.w -= uf[3] * (out[3] - 2.0f * cen[3] + um[3]);
-            *reinterpret_cast<float4*>(g) = gv;
+            *reinterpret_cast<float4*>(gp) = make_float4(g[0], g[1], g[2], g[3]);
         } else {
-            for (int i = 0; i < nvalid; ++i) g[i] -= uf[i] * (out[i] - 2.0f * cen[i] + um[i]);
+            for (int i = 0; i < nvalid; ++i) gp[i] = g[i];
         }
     }
 }
 
-// Sparse part of a step, run by the CTA that owns the tile after its points
-// are written: injection into unew (atomic: taps of different points may
-// share a grid point), then gathers of unew into slots.
-template <bool ADJ>
-__device__ __forceinline__ void sparse_phase(const StepArgs& a, long long tile, long long so, int tid,
-                                             int nthr)
+
+// A thread whose 4 points all lie in the pitch padding [Nx, P) writes zeros
+// there, so that a buffer that is only ever written by steps still reads as
+// the zero exterior.
+__device__ __forceinline__ void zero_padding(const StepArgs& a, long long so, long long off, int gx)
 {
-    float* un = a.unew + so;
-    if (a.inj.tile_start) {
-        const int b = a.inj.tile_start[tile], e = a.inj.tile_start[tile + 1];
-        for (int j = b + tid; j < e; j += nthr) {
-            const int i = a.inj.idx[j];
-            const long long ai = (long long)a.inj.ab[j] + (long long)a.amp_row * a.inj.npts;
-            float amp = a.amp_a[ai];
-            if (a.amp_b) amp -= a.amp_b[ai];
-            const float add = a.inj.fac[j] * amp;
-            atomicAdd(un + i, add);
-            if (ADJ && a.gacc) {
-                const float uf = a.uf16 ? __bfloat162float(a.uf16[so + i]) : a.uf32[so + i];
-                atomicAdd(a.gacc + so + i, -uf * add);
-            }
-        }
-        if (!ADJ && (a.st16 || a.st32)) {
-            // the stored copy of the new level must include the injection
-            __syncthreads();
-            for (int j = b + tid; j < e; j += nthr) {
-                const int i = a.inj.idx[j];
-                const float v = un[i];
-                if (a.st16) a.st16[so + i] = __float2bfloat16_rn(v);
-                if (a.st32) a.st32[so + i] = v;
-            }
-        }
-    }
-    if (a.gat.tile_start) {
-        __syncthreads();
-        const int b = a.gat.tile_start[tile], e = a.gat.tile_start[tile + 1];
-        float* row = a.slots + (long long)a.slot_row * a.gat.ntap;
-        for (int j = b + tid; j < e; j += nthr) row[a.gat.slot[j]] = a.gat.gw[j] * un[a.gat.idx[j]];
-    }
+    if (gx < a.P) *reinterpret_cast<float4*>(a.unew + so + off) = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
-// 2D step.  Tile = 128 (x) by TZ (z) points, CTA = 32 x BZ threads, each
-// thread updates 4 consecutive x points on TZ/BZ rows.  The (TZ+8) x 136 halo
-// tile of u is staged in shared memory with 128-bit loads; values outside the
-// padded grid read as zero.
+// 2D step, direct loads.  Tile = 128 (x) by TZ (z) points, CTA = 32 x BZ
+// threads, each thread updates 4 consecutive x points on TZ/BZ rows.  The
+// (TZ+8) x 136 halo tile of u is staged in shared memory with 128-bit loads;
+// values outside the padded grid read as zero.  The pointwise inputs of the
+// thread's rows are loaded before the halo tile so that their latency overlaps.
 template <int TZ, int BZ, bool ADJ>
 __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
 {
-    constexpr int SW = 136;
+    constexpr int SW = kTX + 8;
+    constexpr int RB = TZ / BZ;
     __shared__ __align__(16) float s[TZ + 8][SW];
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    const int x0 = blockIdx.x * 128, z0 = blockIdx.y * TZ;
-    const long long so = (long long)blockIdx.z * a.cell;
+    const int x0 = blockIdx.x * kTX, z0 = blockIdx.y * TZ;
+    const int shot = blockIdx.z;
+    const long long so = (long long)shot * a.cell;
     const float* __restrict__ u = a.u + so;
+    const int lx = 4 * threadIdx.x;
+    const int gx = x0 + lx;
+    const int nvalid = min(4, a.Nx - gx);
+    const bool imaging = ADJ && a.gacc != nullptr;
 
+    float4 kp[RB], uo[RB];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+        const int gz = z0 + threadIdx.y + rr * BZ;
+        kp[rr] = uo[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gz < a.Nz && nvalid > 0) {
+            const long long off = (long long)gz * a.P + gx;
+            kp[rr] = ld4(a.kap + off);
+            uo[rr] = *reinterpret_cast<const float4*>(a.uprev + so + off);
+        }
+    }
     for (int i = tid; i < (TZ + 8) * (SW / 4); i += 32 * BZ) {
         const int r = i / (SW / 4), c4 = i - r * (SW / 4);
-        const int gz = z0 - 4 + r, gx = x0 - 4 + 4 * c4;
+        const int gz = z0 - 4 + r, gxx = x0 - 4 + 4 * c4;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gz >= 0 && gz < a.Nz && gx >= 0 && gx < a.P) v = ld4(u + (long long)gz * a.P + gx);
+        if (gz >= 0 && gz < a.Nz && gxx >= 0 && gxx < a.P) v = ld4(u + (long long)gz * a.P + gxx);
         *reinterpret_cast<float4*>(&s[r][4 * c4]) = v;
     }
     __syncthreads();
 
-    const int lx = 4 * threadIdx.x;
-    const int gx = x0 + lx;
-    const int nvalid = min(4, a.Nx - gx);
+    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
 #pragma unroll
-    for (int rr = 0; rr < TZ / BZ; ++rr) {
+    for (int rr = 0; rr < RB; ++rr) {
         const int r = threadIdx.y + rr * BZ;
         const int gz = z0 + r;
-        if (gz >= a.Nz || nvalid <= 0) continue;
-        const float* row = &s[r + 4][lx];
-        float w[12];
-        {
-            float4 A = *reinterpret_cast<const float4*>(row);
-            float4 B = *reinterpret_cast<const float4*>(row + 4);
-            float4 C = *reinterpret_cast<const float4*>(row + 8);
-            w[0] = A.x; w[1] = A.y; w[2] = A.z; w[3] = A.w;
-            w[4] = B.x; w[5] = B.y; w[6] = B.z; w[7] = B.w;
-            w[8] = C.x; w[9] = C.y; w[10] = C.z; w[11] = C.w;
+        if (gz >= a.Nz) continue;
+        if (nvalid <= 0) {
+            zero_padding(a, so, (long long)gz * a.P + gx, gx);
+            continue;
         }
+        const float* row = &s[r + 4][lx];
+        const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
+        const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
         float lap[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             lap[i] = 2.0f * kC0 * w[i + 4] + kC1 * (w[i + 3] + w[i + 5]) + kC2 * (w[i + 2] + w[i + 6]) +
                      kC3 * (w[i + 1] + w[i + 7]) + kC4 * (w[i] + w[i + 8]);
-        const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
 #pragma unroll
         for (int k = 1; k <= 4; ++k) {
-            float4 U = *reinterpret_cast<const float4*>(&s[r + 4 - k][lx + 4]);
-            float4 D = *reinterpret_cast<const float4*>(&s[r + 4 + k][lx + 4]);
+            const float4 U = lds4(&s[r + 4 - k][lx + 4]);
+            const float4 D = lds4(&s[r + 4 + k][lx + 4]);
             lap[0] += ck[k] * (U.x + D.x);
             lap[1] += ck[k] * (U.y + D.y);
             lap[2] += ck[k] * (U.z + D.z);
             lap[3] += ck[k] * (U.w + D.w);
         }
         const long long off = (long long)gz * a.P + gx;
-        const float4 kp = ld4(a.kap + off);
-        const float4 uo = *reinterpret_cast<const float4*>(a.unew + so + off);
         const int dz = sponge_depth(gz, a.nb, a.nz);
-        float out[4], cen[4], um[4];
+        float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int dd = max(sponge_depth(gx + i, a.nb, a.nx), dz);
-            const float kap = f4(kp, i);
+            const float kap = f4(kp[rr], i);
             const float eps = kap * a.ceps * (float)(dd * dd);
             cen[i] = w[i + 4];
-            um[i] = f4(uo, i);
+            um[i] = f4(uo[rr], i);
             out[i] = leap(cen[i], um[i], lap[i], kap, eps);
         }
-        finish4<ADJ>(a, so, off, nvalid, out, cen, um);
+        float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (imaging) {
+            if (a.uf16) {
+                unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off), uf);
+            } else {
+                const float4 v = ld4(a.uf32 + so + off);
+                uf[0] = v.x;
+                uf[1] = v.y;
+                uf[2] = v.z;
+                uf[3] = v.w;
+            }
+            gv = *reinterpret_cast<const float4*>(a.gacc + so + off);
+        }
+        write4<ADJ>(a, so, off, nvalid, out, cen, um, imaging, uf, gv);
     }
-    if (a.inj.tile_start || a.gat.tile_start) {
+    if (a.inj.cell_start || a.gat.cell_start) {
         __syncthreads();
-        const long long tile = ((long long)blockIdx.z * a.ntz + blockIdx.y) * a.ntx + blockIdx.x;
-        sparse_phase<ADJ>(a, tile, so, tid, 32 * BZ);
+        const int kcell = TZ / a.TZc;
+        const int cbase = (shot * a.ncx + (int)blockIdx.x) * a.ncz;
+        const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
+        int ib = 0, ie = 0, gb = 0, ge = 0;
+        if (a.inj.cell_start) {
+            ib = a.inj.cell_start[cbase + c0];
+            ie = a.inj.cell_start[cbase + c1];
+        }
+        if (a.gat.cell_start) {
+            gb = a.gat.cell_start[cbase + c0];
+            ge = a.gat.cell_start[cbase + c1];
+        }
+        sparse_phase<ADJ>(a, ib, ie, gb, ge, so, tid, 32 * BZ);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D step: persistent, TMA-fed.  Tile = 128 (x) by TZ (z) points; the CTA has
+// TZ/R warps and warp w owns the R consecutive rows w*R .. w*R+R-1 of a tile,
+// keeping the 9-row z window of its lane's 4 x points in registers (so shared
+// memory is read once per row for the z neighbours).  Per tile one elected
+// thread issues TMA loads of the halo tile of u ((TZ+8) x 136), the previous
+// level, the model and, in the adjoint, the forward field and the gradient
+// accumulators into an NST-deep ring of stages; out-of-range boxes read as
+// zero, which is the Dirichlet exterior.  Results are stored straight from
+// registers.  Tiles are dealt round-robin to the CTAs (one per SM).
+template <int TZ, int R, int NST, bool ADJ>
+__global__ void __launch_bounds__(32 * (TZ / R), 1) k_step2d_tma(const __grid_constant__ StepMaps mp, const StepArgs a)
+{
+    constexpr int NTHR = 32 * (TZ / R);
+    constexpr int SW = kTX + 8;
+    constexpr int SU = (TZ + 8) * SW;  // floats in the halo tile
+    constexpr int ST = TZ * kTX;       // floats in a point tile
+    constexpr int NT = ADJ ? 4 : 2;
+    constexpr int STAGE = SU + NT * ST;
+    static_assert(SU % 32 == 0 && ST % 32 == 0, "sub-buffers must stay 128-byte aligned");
+    extern __shared__ unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bars[NST];
+    float* base = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
+
+    const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
+    const CUtensorMap* mt = ADJ ? &mp.tile_a : &mp.tile_f;
+    const CUtensorMap* mk = ADJ ? &mp.kap_a : &mp.kap_f;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntz = (a.Nz + TZ - 1) / TZ;
+    const int per_shot = ntz * a.ncx;
+    const int ntile = a.nshot * per_shot;
+    const bool imaging = ADJ && a.g_buf >= 0;
+    const bool uf_bf16 = ADJ && a.uf_buf < 0;
+    const uint32_t bytes = (SU + 2 * ST) * 4u + (imaging ? (uf_bf16 ? ST * 2u : ST * 4u) + ST * 4u : 0u);
+    const int kcell = TZ / a.TZc;
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int t) {
+        float* st = base + s * STAGE;
+        const int shot = t / per_shot, r = t - shot * per_shot, tz = r / a.ncx, tx = r - tz * a.ncx;
+        const int x0 = tx * kTX, z0 = tz * TZ;
+        mbar_expect_tx(&bars[s], bytes);
+        tma_load_4d(st, mh, &bars[s], x0 - 4, z0 - 4, shot, a.u_buf);
+        tma_load_4d(st + SU, mt, &bars[s], x0, z0, shot, a.prev_buf);
+        tma_load_2d(st + SU + ST, mk, &bars[s], x0, z0);
+        if (imaging) {
+            if (uf_bf16)
+                tma_load_4d(st + SU + 2 * ST, &mp.tile16_a, &bars[s], x0, z0, shot, a.uf16_row);
+            else
+                tma_load_4d(st + SU + 2 * ST, mt, &bars[s], x0, z0, shot, a.uf_buf);
+            tma_load_4d(st + SU + 3 * ST, mt, &bars[s], x0, z0, shot, a.g_buf);
+        }
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            const int t = blockIdx.x + s * gridDim.x;
+            if (t < ntile) issue(s, t);
+        }
+    }
+
+    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
+    const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
+    for (int i = 0;; ++i) {
+        const int t = blockIdx.x + i * gridDim.x;
+        if (t >= ntile) break;
+        const int s = i % NST;
+        const bool ok = mbar_wait(&bars[s], (uint32_t)(i / NST) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(a.err, kErrTimeout);
+                // let copies still in flight land before the CTA's shared memory is released
+                for (int j = 0; j < NST; ++j) {
+                    const int ii = i + j;
+                    if ((long long)blockIdx.x + (long long)ii * gridDim.x < ntile)
+                        mbar_wait(&bars[ii % NST], (uint32_t)(ii / NST) & 1u);
+                }
+            }
+            return;
+        }
+        const float* su = base + s * STAGE;
+        const float* sp = su + SU;
+        const float* sk = sp + ST;
+        const float* sf = sk + ST;
+        const float* sg = sf + ST;
+        const int shot = t / per_shot, rt = t - shot * per_shot, tz = rt / a.ncx, txi = rt - tz * a.ncx;
+        const int x0 = txi * kTX, z0 = tz * TZ;
+        const int gx = x0 + 4 * lane;
+        const int nvalid = min(4, a.Nx - gx);
+        const long long so = (long long)shot * a.cell;
+        const int r0 = warp * R;
+        float4 q[9];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = lds4(su + (r0 + k) * SW + 4 * lane + 4);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int r = r0 + j;
+            q[8] = lds4(su + (r + 8) * SW + 4 * lane + 4);
+            const int gz = z0 + r;
+            if (gz < a.Nz && nvalid <= 0) zero_padding(a, so, (long long)gz * a.P + gx, gx);
+            if (gz < a.Nz && nvalid > 0) {
+                const float4 A = lds4(su + (r + 4) * SW + 4 * lane);
+                const float4 C = lds4(su + (r + 4) * SW + 4 * lane + 8);
+                const float4 B = q[4];
+                const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+                float lap[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
+                             kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
+#pragma unroll
+                for (int k = 1; k <= 4; ++k) {
+                    lap[0] += ck[k] * (q[4 - k].x + q[4 + k].x);
+                    lap[1] += ck[k] * (q[4 - k].y + q[4 + k].y);
+                    lap[2] += ck[k] * (q[4 - k].z + q[4 + k].z);
+                    lap[3] += ck[k] * (q[4 - k].w + q[4 + k].w);
+                }
+                const float4 kp = lds4(sk + r * kTX + 4 * lane);
+                const float4 uo = lds4(sp + r * kTX + 4 * lane);
+                const int dz = sponge_depth(gz, a.nb, a.nz);
+                float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
+                float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
+                    const float kap = f4(kp, e);
+                    const float eps = kap * a.ceps * (float)(dd * dd);
+                    cen[e] = w[e + 4];
+                    um[e] = f4(uo, e);
+                    out[e] = leap(cen[e], um[e], lap[e], kap, eps);
+                }
+                if (imaging) {
+                    if (uf_bf16) {
+                        unpack_bf16x4(*reinterpret_cast<const uint2*>(
+                                          reinterpret_cast<const __nv_bfloat16*>(sf) + r * kTX + 4 * lane),
+                                      uf);
+                    } else {
+                        const float4 v = lds4(sf + r * kTX + 4 * lane);
+                        uf[0] = v.x;
+                        uf[1] = v.y;
+                        uf[2] = v.z;
+                        uf[3] = v.w;
+                    }
+                    gv = lds4(sg + r * kTX + 4 * lane);
+                }
+                write4<ADJ>(a, so, (long long)gz * a.P + gx, nvalid, out, cen, um, imaging, uf, gv);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+        }
+        __syncthreads();  // stage s has been read and tile t's points are written
+        if (tid == 0) {
+            const int t2 = blockIdx.x + (i + NST) * gridDim.x;
+            if (t2 < ntile) {
+                fence_proxy_async();
+                issue(s, t2);
+            }
+        }
+        if (sparse) {
+            const int cbase = (shot * a.ncx + txi) * a.ncz;  // ncy = 1 in 2D
+            const int c0 = tz * kcell, c1 = min(c0 + kcell, a.ncz);
+            int ib = 0, ie = 0, gb = 0, ge = 0;
+            if (a.inj.cell_start) {
+                ib = a.inj.cell_start[cbase + c0];
+                ie = a.inj.cell_start[cbase + c1];
+            }
+            if (a.gat.cell_start) {
+                gb = a.gat.cell_start[cbase + c0];
+                ge = a.gat.cell_start[cbase + c1];
+            }
+            sparse_phase<ADJ>(a, ib, ie, gb, ge, so, tid, NTHR);
+        }
     }
 }
 
@@ -242,17 +516,19 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
 template <int TY, int TZC, bool ADJ>
 __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
 {
-    constexpr int SW = 136;
+    constexpr int SW = kTX + 8;
     __shared__ __align__(16) float s[TY + 8][SW];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * TY;
-    const int shot = blockIdx.z / a.ntz, tzi = blockIdx.z - shot * a.ntz;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+    const int ntz = (a.Nz + TZC - 1) / TZC;
+    const int shot = blockIdx.z / ntz, tzi = blockIdx.z - shot * ntz;
     const int z0 = tzi * TZC;
     const int gx = x0 + 4 * tx, gy = y0 + ty;
     const long long so = (long long)shot * a.cell;
     const long long plane = (long long)a.Ny * a.P;
     const float* __restrict__ u = a.u + so;
     const int nvalid = min(4, a.Nx - gx);
+    const bool imaging = ADJ && a.gacc != nullptr;
 
     auto ld = [&](int z, int y, int x) -> float4 {
         if (z < 0 || z >= a.Nz || y < 0 || y >= a.Ny || x < 0 || x >= a.P) return make_float4(0.f, 0.f, 0.f, 0.f);
@@ -270,7 +546,7 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
         q[8] = ld(gz + 4, gy, gx);
         *reinterpret_cast<float4*>(&s[ty + 4][4 + 4 * tx]) = q[4];
         if (tx == 0) *reinterpret_cast<float4*>(&s[ty + 4][0]) = ld(gz, gy, x0 - 4);
-        if (tx == 31) *reinterpret_cast<float4*>(&s[ty + 4][132]) = ld(gz, gy, x0 + 128);
+        if (tx == 31) *reinterpret_cast<float4*>(&s[ty + 4][132]) = ld(gz, gy, x0 + kTX);
         for (int i = tid; i < 8 * (SW / 4); i += 32 * TY) {
             const int r = i / (SW / 4), c4 = i - r * (SW / 4);
             const int yy = r < 4 ? y0 - 4 + r : y0 + TY + (r - 4);
@@ -278,17 +554,11 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
             *reinterpret_cast<float4*>(&s[sr][4 * c4]) = ld(gz, yy, x0 - 4 + 4 * c4);
         }
         __syncthreads();
+        if (gy < a.Ny && nvalid <= 0) zero_padding(a, so, gz * plane + (long long)gy * a.P + gx, gx);
         if (gy < a.Ny && nvalid > 0) {
             const float* row = &s[ty + 4][4 * tx];
-            float w[12];
-            {
-                float4 A = *reinterpret_cast<const float4*>(row);
-                float4 B = *reinterpret_cast<const float4*>(row + 4);
-                float4 C = *reinterpret_cast<const float4*>(row + 8);
-                w[0] = A.x; w[1] = A.y; w[2] = A.z; w[3] = A.w;
-                w[4] = B.x; w[5] = B.y; w[6] = B.z; w[7] = B.w;
-                w[8] = C.x; w[9] = C.y; w[10] = C.z; w[11] = C.w;
-            }
+            const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -296,8 +566,8 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
                          kC3 * (w[i + 1] + w[i + 7]) + kC4 * (w[i] + w[i + 8]);
 #pragma unroll
             for (int k = 1; k <= 4; ++k) {
-                float4 U = *reinterpret_cast<const float4*>(&s[ty + 4 - k][4 * tx + 4]);
-                float4 D = *reinterpret_cast<const float4*>(&s[ty + 4 + k][4 * tx + 4]);
+                const float4 U = lds4(&s[ty + 4 - k][4 * tx + 4]);
+                const float4 D = lds4(&s[ty + 4 + k][4 * tx + 4]);
                 const float4 zu = q[4 - k], zd = q[4 + k];
                 lap[0] += ck[k] * (U.x + D.x + zu.x + zd.x);
                 lap[1] += ck[k] * (U.y + D.y + zu.y + zd.y);
@@ -306,9 +576,9 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
             }
             const long long off = gz * plane + (long long)gy * a.P + gx;
             const float4 kp = ld4(a.kap + off);
-            const float4 uo = *reinterpret_cast<const float4*>(a.unew + so + off);
+            const float4 uo = *reinterpret_cast<const float4*>(a.uprev + so + off);
             const int dzy = max(sponge_depth(gz, a.nb, a.nz), sponge_depth(gy, a.nb, a.ny));
-            float out[4], cen[4], um[4];
+            float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int dd = max(sponge_depth(gx + i, a.nb, a.nx), dzy);
@@ -318,52 +588,145 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
                 um[i] = f4(uo, i);
                 out[i] = leap(cen[i], um[i], lap[i], kap, eps);
             }
-            finish4<ADJ>(a, so, off, nvalid, out, cen, um);
+            float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (imaging) {
+                if (a.uf16) {
+                    unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off), uf);
+                } else {
+                    const float4 v = ld4(a.uf32 + so + off);
+                    uf[0] = v.x;
+                    uf[1] = v.y;
+                    uf[2] = v.z;
+                    uf[3] = v.w;
+                }
+                gv = *reinterpret_cast<const float4*>(a.gacc + so + off);
+            }
+            write4<ADJ>(a, so, off, nvalid, out, cen, um, imaging, uf, gv);
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
     }
-    if (a.inj.tile_start || a.gat.tile_start) {
-        const long long tile = (((long long)shot * a.ntz + tzi) * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
-        sparse_phase<ADJ>(a, tile, so, tid, 32 * TY);
+    if (a.inj.cell_start || a.gat.cell_start) {
+        const int kcell = TZC / a.TZc;
+        const int cbase = ((shot * a.ncx + (int)blockIdx.x) * a.ncy + (int)blockIdx.y) * a.ncz;
+        const int c0 = tzi * kcell, c1 = min(c0 + kcell, a.ncz);
+        int ib = 0, ie = 0, gb = 0, ge = 0;
+        if (a.inj.cell_start) {
+            ib = a.inj.cell_start[cbase + c0];
+            ie = a.inj.cell_start[cbase + c1];
+        }
+        if (a.gat.cell_start) {
+            gb = a.gat.cell_start[cbase + c0];
+            ge = a.gat.cell_start[cbase + c1];
+        }
+        sparse_phase<ADJ>(a, ib, ie, gb, ge, so, tid, 32 * TY);
     }
 }
 
-static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, int nshot, const StepArgs& a, cudaStream_t s);
+// ---------------------------------------------------------------------------
 
-void launch_step(const Tiling& t, int ndim, bool adjoint, int nshot, const StepArgs& a, cudaStream_t s)
+static int num_sms()
 {
-    count_launch();
-    cudaEvent_t stop;
-    const bool timed = profile_sample(adjoint, s, &stop);
-    launch_step_raw(t, ndim, adjoint, nshot, a, s);
-    if (timed) profile_close(stop, s);
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        n = v;
+    }
+    return n;
 }
 
-static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, int nshot, const StepArgs& a, cudaStream_t s)
+template <int TZ, int R, int NST, bool ADJ>
+static void launch_2d(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+{
+    constexpr int STAGE = (TZ + 8) * (kTX + 8) + (ADJ ? 4 : 2) * TZ * kTX;
+    constexpr size_t smem = (size_t)NST * STAGE * 4 + 128;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_step2d_tma<TZ, R, NST, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    const int ntz = (a.Nz + TZ - 1) / TZ;
+    const long long ntile = (long long)a.nshot * ntz * a.ncx;
+    const int grid = (int)std::min<long long>(ntile, num_sms());
+    k_step2d_tma<TZ, R, NST, ADJ><<<grid, 32 * (TZ / R), smem, s>>>(*maps, a);
+}
+
+// 2D variants (which = 0 forward, 1 adjoint).  The TMA map boxes and the
+// launch below must agree on TZ; plan/api read TZ from this table.
+static const Variant2D kFwd2D[] = {{0, 32, 4, 0}, {1, 48, 6, 2}, {1, 32, 4, 3}, {1, 24, 3, 4}, {1, 16, 2, 4},
+                                   {1, 32, 2, 3}};
+static const Variant2D kAdj2D[] = {{0, 32, 4, 0}, {1, 24, 3, 3}, {1, 16, 2, 4}, {1, 32, 4, 2}};
+static int g_selected[2] = {-1, -1};
+static const int kDefault2D[2] = {0, 0};
+
+int variant_count(int which) { return which == 0 ? 6 : (which == 1 ? 4 : 0); }
+
+Variant2D variant_info(int which, int v)
+{
+    if (v < 0 || v >= variant_count(which)) return Variant2D{-1, 0, 0, 0};
+    return which == 0 ? kFwd2D[v] : kAdj2D[v];
+}
+
+int current_variant(int which)
+{
+    if (which < 0 || which > 1) return -1;
+    return g_selected[which] >= 0 ? g_selected[which] : kDefault2D[which];
+}
+
+int select_variant(int which, int v)
+{
+    if (which < 0 || which > 1 || v < -1 || v >= variant_count(which)) return -1;
+    g_selected[which] = v;
+    return 0;
+}
+
+template <int TZ, int BZ, bool ADJ>
+static void launch_2d_direct(const StepArgs& a, cudaStream_t s)
+{
+    dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, a.nshot);
+    k_step2d<TZ, BZ, ADJ><<<grid, dim3(32, BZ), 0, s>>>(a);
+}
+
+static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepArgs& a, const StepMaps* maps,
+                            cudaStream_t s)
 {
     if (ndim == 2) {
-        dim3 grid(t.ntx, t.ntz, nshot);
-        if (t.TZ == 32) {
-            dim3 block(32, 8);
-            if (adjoint) k_step2d<32, 8, true><<<grid, block, 0, s>>>(a);
-            else k_step2d<32, 8, false><<<grid, block, 0, s>>>(a);
-        } else if (t.TZ == 16) {
-            dim3 block(32, 8);
-            if (adjoint) k_step2d<16, 8, true><<<grid, block, 0, s>>>(a);
-            else k_step2d<16, 8, false><<<grid, block, 0, s>>>(a);
+        if (!adjoint) {
+            switch (t.vf) {
+            case 1: launch_2d<48, 6, 2, false>(a, maps, s); break;
+            case 2: launch_2d<32, 4, 3, false>(a, maps, s); break;
+            case 3: launch_2d<24, 3, 4, false>(a, maps, s); break;
+            case 4: launch_2d<16, 2, 4, false>(a, maps, s); break;
+            case 5: launch_2d<32, 2, 3, false>(a, maps, s); break;
+            default: launch_2d_direct<32, 8, false>(a, s); break;
+            }
         } else {
-            dim3 block(32, 8);
-            if (adjoint) k_step2d<64, 8, true><<<grid, block, 0, s>>>(a);
-            else k_step2d<64, 8, false><<<grid, block, 0, s>>>(a);
+            switch (t.va) {
+            case 1: launch_2d<24, 3, 3, true>(a, maps, s); break;
+            case 2: launch_2d<16, 2, 4, true>(a, maps, s); break;
+            case 3: launch_2d<32, 4, 2, true>(a, maps, s); break;
+            default: launch_2d_direct<32, 8, true>(a, s); break;
+            }
         }
     } else {
-        dim3 grid(t.ntx, t.nty, t.ntz * nshot);
+        const int ntz = (a.Nz + 31) / 32;
+        dim3 grid(t.ncx, t.ncy, ntz * a.nshot);
         dim3 block(32, 8);
         if (adjoint) k_step3d<8, 32, true><<<grid, block, 0, s>>>(a);
         else k_step3d<8, 32, false><<<grid, block, 0, s>>>(a);
     }
+}
+
+void launch_step(const Tiling& t, int ndim, bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+{
+    count_launch();
+    cudaEvent_t stop;
+    const bool timed = profile_sample(adjoint, s, &stop);
+    launch_step_raw(t, ndim, adjoint, a, maps, s);
+    if (timed) profile_close(stop, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -430,13 +793,13 @@ void launch_tapfac(const Dims& d, const TapList& l, const float* kap, float scal
 {
     if (l.ntap == 0) return;
     count_launch();
-    k_tapfac<<<(l.ntap + 255) / 256, 256, 0, s>>>(d, l.ntap, l.idx, l.w, const_cast<float*>(l.fac), kap,
-                                                   scale_inj, ceps);
+    k_tapfac<<<(l.ntap + 255) / 256, 256, 0, s>>>(d, l.ntap, l.idx, l.w, const_cast<float*>(l.fac), kap, scale_inj,
+                                                   ceps);
 }
 
 // out[s][n][p] = sum of the point's gather slots at time row n.
-__global__ void k_finalize(const int* __restrict__ pt_start, const float* __restrict__ slots, int npts_all,
-                           int npts, int nt, int ntap, float* __restrict__ out)
+__global__ void k_finalize(const int* __restrict__ pt_start, const float* __restrict__ slots, int npts_all, int npts,
+                           int nt, int ntap, float* __restrict__ out)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long total = (long long)nt * npts_all;
@@ -499,38 +862,66 @@ void launch_misfit(const float* a, const float* b, long long n, double* partial,
     k_sum_partial<<<1, 256, 0, s>>>(partial, npart, out);
 }
 
-// grad[j] = sum over shots and over the padded cells whose model value was
-// copied from physical cell j (the adjoint of the edge extension).
-__global__ void k_grad_reduce(Dims d, const float* __restrict__ gacc, int nshot, float* __restrict__ grad)
+// Gradient on the physical grid: sum over shots, then the adjoint of the
+// edge-replicating extension one axis at a time (each physical edge cell
+// collects the sponge cells that were copied from it).
+__global__ void k_shot_sum(const float* __restrict__ gacc, long long cell, int nshot, float* __restrict__ out)
 {
-    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (j >= d.phys) return;
-    const int jx = (int)(j % d.nx);
-    const long long r = j / d.nx;
-    const int nyp = d.ndim == 3 ? d.ny : 1;
-    const int jy = (int)(r % nyp);
-    const int jz = (int)(r / nyp);
-    const int x_lo = jx == 0 ? 0 : jx + d.nb, x_hi = jx == d.nx - 1 ? d.Nx - 1 : jx + d.nb;
-    const int z_lo = jz == 0 ? 0 : jz + d.nb, z_hi = jz == d.nz - 1 ? d.Nz - 1 : jz + d.nb;
-    int y_lo = 0, y_hi = 0;
-    if (d.ndim == 3) {
-        y_lo = jy == 0 ? 0 : jy + d.nb;
-        y_hi = jy == d.ny - 1 ? d.Ny - 1 : jy + d.nb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cell; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int s = 0; s < nshot; ++s) acc += gacc[(long long)s * cell + i];
+        out[i] = acc;
     }
-    float acc = 0.0f;
-    for (int s = 0; s < nshot; ++s) {
-        const float* g = gacc + (long long)s * d.cell;
-        for (int z = z_lo; z <= z_hi; ++z)
-            for (int y = y_lo; y <= y_hi; ++y)
-                for (int x = x_lo; x <= x_hi; ++x) acc += g[((long long)z * d.Ny + y) * d.P + x];
-    }
-    grad[j] = acc;
 }
 
-void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* grad, cudaStream_t s)
+// in [rows][P] (padded x) -> out [rows][nx]
+__global__ void k_collapse_x(const float* __restrict__ in, long long rows, int P, int nx, int nb, int Nx,
+                             float* __restrict__ out)
 {
-    count_launch();
-    k_grad_reduce<<<(int)((d.phys + 255) / 256), 256, 0, s>>>(d, gacc, nshot, grad);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * nx) return;
+    const int jx = (int)(i % nx);
+    const long long r = i / nx;
+    const int lo = jx == 0 ? 0 : jx + nb, hi = jx == nx - 1 ? Nx - 1 : jx + nb;
+    float acc = 0.0f;
+    for (int x = lo; x <= hi; ++x) acc += in[r * P + x];
+    out[i] = acc;
+}
+
+// in [outer][N][M] (padded middle axis) -> out [outer][n][M]
+__global__ void k_collapse_mid(const float* __restrict__ in, long long outer, int N, int n, int nb, long long M,
+                               float* __restrict__ out)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= outer * n * M) return;
+    const long long m = i % M;
+    const long long r = i / M;
+    const int j = (int)(r % n);
+    const long long o = r / n;
+    const int lo = j == 0 ? 0 : j + nb, hi = j == n - 1 ? N - 1 : j + nb;
+    float acc = 0.0f;
+    for (int k = lo; k <= hi; ++k) acc += in[(o * N + k) * M + m];
+    out[i] = acc;
+}
+
+void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp, float* grad, cudaStream_t s)
+{
+    // tmp holds 2 * cell floats: [0, cell) the shot sum, [cell, 2 cell) the x-collapsed sum.
+    float* t0 = tmp;
+    float* t1 = tmp + d.cell;
+    const int bs = 256;
+    count_launch(d.ndim == 3 ? 4 : 3);
+    k_shot_sum<<<152 * 8, bs, 0, s>>>(gacc, d.cell, nshot, t0);
+    const long long rows = (long long)d.Nz * d.Ny;
+    k_collapse_x<<<(int)((rows * d.nx + bs - 1) / bs), bs, 0, s>>>(t0, rows, d.P, d.nx, d.nb, d.Nx, t1);
+    if (d.ndim == 3) {
+        const long long n1 = (long long)d.Nz * d.ny * d.nx;
+        k_collapse_mid<<<(int)((n1 + bs - 1) / bs), bs, 0, s>>>(t1, d.Nz, d.Ny, d.ny, d.nb, d.nx, t0);
+        k_collapse_mid<<<(int)((d.phys + bs - 1) / bs), bs, 0, s>>>(t0, 1, d.Nz, d.nz, d.nb,
+                                                                     (long long)d.ny * d.nx, grad);
+    } else {
+        k_collapse_mid<<<(int)((d.phys + bs - 1) / bs), bs, 0, s>>>(t1, 1, d.Nz, d.nz, d.nb, d.nx, grad);
+    }
 }
 
 __global__ void k_ricker(double f0, double dt, int nt, float* out)

@@ -31,23 +31,23 @@ Dims make_dims(const wave_grid_t& g)
     return d;
 }
 
-Tiling choose_tiling(const Dims& d, int nshot)
+Tiling choose_tiling(const Dims& d)
 {
-    (void)nshot;
     Tiling t;
-    t.TX = 128;
+    t.TX = kTX;
+    t.vf = t.va = -1;
     if (d.ndim == 2) {
         t.TY = 1;
-        t.TZ = 32;
-        t.kind = 0;
+        t.TZc = kTZc2;
+        t.vf = current_variant(0);
+        t.va = current_variant(1);
     } else {
         t.TY = 8;
-        t.TZ = 32;
-        t.kind = 1;
+        t.TZc = 32;
     }
-    t.ntx = (d.Nx + t.TX - 1) / t.TX;
-    t.nty = (d.Ny + t.TY - 1) / t.TY;
-    t.ntz = (d.Nz + t.TZ - 1) / t.TZ;
+    t.ncx = (d.Nx + t.TX - 1) / t.TX;
+    t.ncy = (d.Ny + t.TY - 1) / t.TY;
+    t.ncz = (d.Nz + t.TZc - 1) / t.TZc;
     return t;
 }
 
@@ -107,13 +107,13 @@ wave_status_t build_taps(const Dims& d, const Tiling& t, int nshot, int npts, co
 {
     out = HostTaps();
     out.npts = npts;
-    const long long tps = t.tiles_per_shot();
+    const long long cps = t.cells_per_shot();
     const long long npts_all = (long long)nshot * npts;
-    std::vector<int> tile_of;
+    std::vector<int> cell_of;
     std::vector<int> idx_pt, ab_pt;
     std::vector<float> w_pt;
     out.pt_start.resize(npts_all + 1);
-    tile_of.reserve(npts_all * 2);
+    cell_of.reserve(npts_all * 2);
     int tmp_idx[8];
     float tmp_w[8];
     for (int s = 0; s < nshot; ++s) {
@@ -128,8 +128,9 @@ wave_status_t build_taps(const Dims& d, const Tiling& t, int nshot, int npts, co
                 const int r = i / d.P;
                 const int y = r % d.Ny;
                 const int z = r / d.Ny;
-                const long long tile = ((long long)(z / t.TZ) * t.nty + (y / t.TY)) * t.ntx + (x / t.TX);
-                tile_of.push_back((int)(s * tps + tile));
+                // cells in (shot, cx, cy, cz) order with cz fastest
+                const long long cell = (((long long)s * t.ncx + x / t.TX) * t.ncy + y / t.TY) * t.ncz + z / t.TZc;
+                cell_of.push_back((int)cell);
                 idx_pt.push_back(i);
                 w_pt.push_back(tmp_w[k]);
                 ab_pt.push_back((int)((long long)s * d.nt * npts + p));
@@ -138,21 +139,28 @@ wave_status_t build_taps(const Dims& d, const Tiling& t, int nshot, int npts, co
     }
     out.pt_start[npts_all] = (int)idx_pt.size();
     const size_t ntap = idx_pt.size();
-    // Stable counting sort of the taps by (shot, tile).
-    out.tile_start.assign(nshot * tps + 1, 0);
-    for (size_t j = 0; j < ntap; ++j) out.tile_start[tile_of[j] + 1]++;
-    for (long long i = 0; i < nshot * tps; ++i) out.tile_start[i + 1] += out.tile_start[i];
-    std::vector<int> fill(out.tile_start.begin(), out.tile_start.end() - 1);
+    // Stable counting sort of the taps by cell.
+    out.cell_start.assign(nshot * cps + 1, 0);
+    for (size_t j = 0; j < ntap; ++j) out.cell_start[cell_of[j] + 1]++;
+    for (long long i = 0; i < nshot * cps; ++i) out.cell_start[i + 1] += out.cell_start[i];
+    std::vector<int> fill(out.cell_start.begin(), out.cell_start.end() - 1);
     out.idx.resize(ntap);
     out.w.resize(ntap);
     out.ab.resize(ntap);
     out.slot.resize(ntap);
-    for (size_t j = 0; j < ntap; ++j) {
-        const int pos = fill[tile_of[j]]++;
+    std::vector<int> order(ntap);
+    for (size_t j = 0; j < ntap; ++j) order[fill[cell_of[j]]++] = (int)j;
+    // Inside a cell, taps of the same grid point become adjacent (stable by
+    // point order), so one thread can own each injected point.
+    for (long long c = 0; c < nshot * cps; ++c)
+        std::stable_sort(order.begin() + out.cell_start[c], order.begin() + out.cell_start[c + 1],
+                         [&](int x, int y) { return idx_pt[x] < idx_pt[y]; });
+    for (size_t pos = 0; pos < ntap; ++pos) {
+        const int j = order[pos];
         out.idx[pos] = idx_pt[j];
         out.w[pos] = w_pt[j];
         out.ab[pos] = ab_pt[j];
-        out.slot[pos] = (int)j;
+        out.slot[pos] = j;
     }
     return WAVE_OK;
 }

@@ -79,6 +79,10 @@ def _lib():
         lib.wave_status_str.restype = ctypes.c_char_p
         lib.wave_forward_static.argtypes = [G, P, I, I, P, P, I, P, P, P]
         lib.wave_forward_static.restype = I
+        lib.wave_set_variant.argtypes = [I, I]
+        lib.wave_set_variant.restype = I
+        lib.wave_variant_count.argtypes = [I]
+        lib.wave_variant_count.restype = I
         lib.wave_profile_start.argtypes = [I]
         lib.wave_profile_stop.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -309,3 +313,14 @@ def wave_profile_stop():
     if st:
         raise WaveError(st, "wave_profile_stop")
     return f.value, nf.value, a.value, na.value
+
+
+def wave_set_variant(which: int, variant: int) -> None:
+    """Select the 2D forward (which=0) or adjoint (which=1) kernel variant; -1 = default."""
+    st = _lib().wave_set_variant(int(which), int(variant))
+    if st:
+        raise WaveError(st, "wave_set_variant")
+
+
+def wave_variant_count(which: int) -> int:
+    return int(_lib().wave_variant_count(int(which)))

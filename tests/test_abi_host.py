@@ -28,7 +28,7 @@ def declared_functions():
     for h in os.listdir(os.path.join(ROOT, "include")):
         if h.endswith(".h"):
             text = open(os.path.join(ROOT, "include", h)).read()
-            names += re.findall(r"^\s*(?:wave_status_t|double|long long|const char\*)\s+(wave_\w+)\s*\(", text, re.M)
+            names += re.findall(r"^\s*(?:wave_status_t|double|long long|int|const char\*)\s+(wave_\w+)\s*\(", text, re.M)
     return sorted(set(names))
 
 
@@ -62,7 +62,7 @@ def test_workspace_grows_with_store_and_snapshots():
     assert 0 < f and 0 < a < c4 < c8 < b16 < f32
     # padded fields: (nz+2nb) x pitch(nx+2nb) floats per shot
     cell = (p.nz + 2 * p.nb) * ((p.nx + 2 * p.nb + 31) // 32 * 32)
-    assert f32 - b16 >= p.nt * p.nshot * cell * 2
+    assert f32 - b16 >= p.nt * p.nshot * cell * 2 - 4096  # up to alignment padding
 
 
 def test_geometry_outside_grid_is_rejected_before_launch():
