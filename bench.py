@@ -36,10 +36,7 @@ WORKLOAD = ("2D FWI gradient, 32 shots: 512x256 at 6.25 m, layered 1500-3500 m/s
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # the SHA-256 of the kernel source they were taken on; dropped (null) once the source changes.
-TRAFFIC = {
-    ("k_step2d<32,8,false>", "f1417c940da007d6"): 54.24e6,  # profiles/k_step2d_config2_gradient.md
-    ("k_step2d<32,8,true>", "f1417c940da007d6"): 115.45e6,
-}
+TRAFFIC = {}
 
 
 def parse():
@@ -211,6 +208,7 @@ def main():
     wavelet = q1[None, :, None].repeat(p.nshot, 1, 1).contiguous()
     d_obs = wave.wave_forward(grid, vel_true, p.src, wavelet, p.rec)
     store = wave.STORE_CHECKPOINT
+    tuned = wave.wave_autotune(grid, vel, p.src, wavelet, p.rec, steps=40)
     nbytes = wave.wave_workspace_size(grid, wave.OP_GRADIENT, p.src, p.rec, store, args.nsnap)
     work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     grad = torch.empty(grid.phys_shape, dtype=torch.float32, device=dev)
@@ -260,9 +258,9 @@ def main():
     n_fwd_launch = sched_steps * args.steps
     n_adj_launch = (p.nt - 1) * args.steps
     pts = N * p.nshot
-    kern = {"fwd": {"name": "k_step2d<32,8,false>", "bytes": 16 * pts, "avg_s": f_avg,
+    kern = {"fwd": {"name": f"2D forward step, variant {tuned[0]}", "bytes": 16 * pts, "avg_s": f_avg,
                     "total_s": f_avg * n_fwd_launch, "launches": n_fwd_launch},
-            "adj": {"name": "k_step2d<32,8,true>", "bytes": 28 * pts, "avg_s": a_avg,
+            "adj": {"name": f"2D adjoint step + imaging, variant {tuned[1]}", "bytes": 28 * pts, "avg_s": a_avg,
                     "total_s": a_avg * n_adj_launch, "launches": n_adj_launch}}
     dom = max(kern, key=lambda k: kern[k]["total_s"])
     kd = kern[dom]
@@ -283,6 +281,7 @@ def main():
             "config": {"workload": WORKLOAD, "nshot_per_gpu": p.nshot, "nt": p.nt, "grid": f"{p.nx}x{p.nz}",
                        "padded_points": N, "store": "checkpoint", "nsnap": args.nsnap,
                        "forward_steps_per_gradient": sched_steps,
+                       "kernel_variants": {"forward": tuned[0], "adjoint": tuned[1], "chosen_by": "wave_autotune"},
                        "l2": "inputs larger than L2 (d_obs %.0f MB, checkpoints %.1f GB per GPU)" % (
                            d_obs.numel() * 4 / 1e6, nbytes / 1e9),
                        "parallelism": f"shots x{world}, gradient all-reduce" if world > 1 else "single GPU"},

@@ -188,6 +188,19 @@ wave_status_t wave_profile_stop(double* fwd_ms, long long* fwd_n, double* adj_ms
 wave_status_t wave_set_variant(int which, int variant);
 int wave_variant_count(int which);
 
+/* Autotuner for the 2D step kernels (no counterpart in the paper): times
+ * `steps` forward steps (sources, receivers gathered) and `steps` adjoint
+ * steps (imaging on) of every variant on this exact problem, with CUDA events
+ * on `stream`, and records the fastest pair for (padded grid, nshot); later
+ * calls on the same grid and shot count use it unless wave_set_variant forces
+ * a variant.  Arguments as in wave_gradient (the workspace must be sized for
+ * op 2, WAVE_STORE_CHECKPOINT, nsnap = 1 or more); the field buffers of the
+ * workspace are overwritten.  best_fwd / best_adj (host out, may be NULL)
+ * receive the chosen variants (-1 for 3D grids, which have one kernel). */
+wave_status_t wave_autotune(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                            const float* wavelet, int nrec, const float* rec_xyz, int steps, void* work,
+                            size_t work_bytes, void* stream, int* best_fwd, int* best_adj);
+
 /* Largest stable dt * vmax / h for ndim = 2 or 3 (0 for other ndim). */
 double wave_courant_limit(int ndim);
 

@@ -125,7 +125,7 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
     if (op == 2 && (store < 0 || store > 2 || (store == WAVE_STORE_CHECKPOINT && nsnap < 1))) return WAVE_ERR_ARG;
     if ((long long)nshot * g->nt * std::max(nsrc, nrec) >= (1LL << 31)) return WAVE_ERR_ARG;
     L.d = make_dims(*g);
-    L.t = choose_tiling(L.d);
+    L.t = choose_tiling(L.d, nshot);
     L.op = op;
     L.nshot = nshot;
     L.nsrc = nsrc;
@@ -651,7 +651,7 @@ wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot
         if (st) return st;
     }
     // A0 and A1 (contiguous) are free now: scratch for the reduction.
-    launch_grad_reduce(d, L.buf(L.iG), nshot, L.buf(A0), grad, s);
+    launch_grad_reduce(d, L.buf(L.iG), gradient_accumulators(L.t, d.ndim, nshot), L.buf(A0), grad, s);
     launch_nan_scan(grad, d.phys, L.err, s);
     if (d_syn && ndata) CK(cudaMemcpyAsync(d_syn, L.dsyn, ndata * sizeof(float), cudaMemcpyDeviceToDevice, s));
     double hm = 0.0;
@@ -668,6 +668,79 @@ wave_status_t wave_ricker(float f0, float dt, int nt, float* out, void* stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     launch_ricker(f0, dt, nt, out, s);
     CK(cudaGetLastError());
+    return WAVE_OK;
+}
+
+wave_status_t wave_autotune(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                            const float* wavelet, int nrec, const float* rec_xyz, int steps, void* work,
+                            size_t work_bytes, void* stream, int* best_fwd, int* best_adj)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (steps < 1 || nshot < 1) return WAVE_ERR_ARG;
+    Layout L;
+    wave_status_t st = plan(grid, 2, nshot, nsrc, src_xyz, nrec, rec_xyz, WAVE_STORE_CHECKPOINT, 1, work, L);
+    if (st) return st;
+    if (!vel || (nsrc && !wavelet)) return WAVE_ERR_ARG;
+    if ((st = check_work(L, work, work_bytes))) return st;
+    if ((st = setup(L, vel, s))) return st;
+    if (L.d.ndim != 2) {
+        // one 3D kernel: nothing to choose
+        if (best_fwd) *best_fwd = -1;
+        if (best_adj) *best_adj = -1;
+        return finish(L, s);
+    }
+    const size_t fb = L.field() * sizeof(float);
+    CK(cudaMemsetAsync(L.buf(0), 0, 6 * fb, s));
+    const size_t nrow = L.hr.idx.size();
+    if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, (size_t)L.d.nt * nrow * sizeof(float), s));
+    CK(cudaMemsetAsync(L.dsyn, 0, (size_t)nshot * L.d.nt * nrec * sizeof(float), s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int nstep = std::max(1, std::min(steps, L.d.nt - 1));
+    float best[2] = {1e30f, 1e30f};
+    int pick[2] = {current_variant(0), current_variant(1)};
+    for (int which = 0; which < 2; ++which) {
+        for (int v = 0; v < variant_count(which); ++v) {
+            if (which == 0) L.t.vf = v;
+            else L.t.va = v;
+            if (make_maps(L)) continue;
+            auto run = [&](int n_steps) {
+                for (int k = 0; k < n_steps; ++k) {
+                    const int n = k % std::max(1, L.d.nt - 1);
+                    if (which == 0) fwd_step(L, L.iW0 + (k & 1), L.iW0 + 1 - (k & 1), L.iW0 + 1 - (k & 1), n, wavelet,
+                                             true, nullptr, nullptr, s);
+                    else adj_step(L, L.iA0 + (k & 1), L.iA0 + 1 - (k & 1), std::max(1, n), L.dsyn, nullptr, false,
+                                  L.iW0, -1, s);
+                }
+            };
+            run(2);
+            cudaEventRecord(e0, s);
+            run(nstep);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                (void)cudaGetLastError();
+                return WAVE_ERR_CUDA;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best[which]) {
+                best[which] = ms;
+                pick[which] = v;
+            }
+        }
+        if (which == 0) L.t.vf = pick[0];
+        else L.t.va = pick[1];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st = finish(L, s);
+    if (st) return st;
+    remember_tuning(L.d, nshot, pick[0], pick[1]);
+    if (best_fwd) *best_fwd = pick[0];
+    if (best_adj) *best_adj = pick[1];
     return WAVE_OK;
 }
 

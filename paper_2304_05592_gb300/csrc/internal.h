@@ -134,15 +134,22 @@ void launch_nan_scan(const float* a, long long n, int* err, cudaStream_t s);
 constexpr int kTX = 128;          // x points per tile (32 lanes x 4)
 constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile height
 
-// 2D kernel variants: direct loads (kind 0) or the persistent TMA pipeline
-// (kind 1) with tile height TZ, R rows per warp and NST stages.
+// 2D kernel variants: direct loads (kind 0), the persistent TMA pipeline
+// (kind 1) with tile height TZ, R rows per warp and NST stages, shot groups
+// (kind 2): one CTA runs its tile for G shots (R = thread rows), or the
+// z-march (kind 3): one warp per TZ-row strip, R warps per CTA, prefetch
+// distance NST rows.  With kind 2
+// in the adjoint, the gradient buffer holds one accumulator per shot group.
 struct Variant2D {
-    int kind, TZ, R, NST;
+    int kind, TZ, R, NST, G;
 };
+// Number of per-shot/per-group gradient accumulators the adjoint step fills.
+int gradient_accumulators(const struct Tiling& t, int ndim, int nshot);
 int variant_count(int which);             // which: 0 forward, 1 adjoint
 Variant2D variant_info(int which, int v);
 int current_variant(int which);           // the selected or default variant
 int select_variant(int which, int v);     // v = -1 restores the default; 0 on success
+bool variant_forced(int which);           // true after wave_set_variant(which, v >= 0)
 
 // Launch accounting and sampled per-launch timing of the stencil kernels
 // (profile.cu).  Every launcher above calls count_launch(); launch_step wraps
@@ -151,8 +158,10 @@ void count_launch(int n = 1);
 bool profile_sample(bool adjoint, cudaStream_t s, cudaEvent_t* stop);
 void profile_close(cudaEvent_t stop, cudaStream_t s);
 
-// Tiling choice (plan.cu).
-Tiling choose_tiling(const Dims& d);
+// Tiling choice (plan.cu): the 2D variants come from wave_set_variant, else
+// from a wave_autotune result for this (grid, nshot), else the defaults.
+Tiling choose_tiling(const Dims& d, int nshot);
+void remember_tuning(const Dims& d, int nshot, int vf, int va);
 
 // Binomial checkpoint schedule (plan.cu).
 enum ActionKind { kAdvance = 0, kSave = 1, kRestore = 2, kAdjointPair = 3, kFinalize = 4 };

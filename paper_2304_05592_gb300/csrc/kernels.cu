@@ -123,13 +123,25 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, uin
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Sparse part of a step, run by the CTA that owns a tile after its points are
-// written: injection into unew, then gathers of unew into slots.  [ib, ie) and [gb, ge) are the
-// tile's ranges in the injection and gather tap lists.
-template <bool ADJ>
+// written: injection into unew, then gathers of unew into slots.  [ib, ie)
+// and [gb, ge) are the tile's ranges in the injection and gather tap lists;
+// sgt, if given, is the tile's gradient accumulator in shared memory, with
+// its first point at (z0, x0).  WARP: the caller is one warp that owns the
+// tile (warp barrier instead of a block barrier).
+template <bool ADJ, bool WARP = false>
 __device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, int gb, int ge, long long so, int tid,
-                                             int nthr)
+                                             int nthr, float* sgt = nullptr, int z0 = 0, int x0 = 0)
 {
     float* un = a.unew + so;
     if (a.inj.cell_start) {
@@ -154,12 +166,19 @@ __device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, 
                 if (a.st32) a.st32[so + i] = v;
             } else if (a.gacc) {
                 const float uf = a.uf16 ? __bfloat162float(a.uf16[so + i]) : a.uf32[so + i];
-                a.gacc[so + i] -= uf * add;
+                if (sgt) {
+                    // the tile's gradient accumulator lives in shared memory (2D, shot-group kernel)
+                    const int z = i / a.P, x = i - z * a.P;
+                    sgt[(z - z0) * kTX + (x - x0)] -= uf * add;
+                } else {
+                    a.gacc[so + i] -= uf * add;
+                }
             }
         }
     }
     if (a.gat.cell_start) {
-        __syncthreads();
+        if (WARP) __syncwarp();
+        else __syncthreads();
         float* row = a.slots + (long long)a.slot_row * a.gat.ntap;
         for (int j = gb + tid; j < ge; j += nthr) row[a.gat.slot[j]] = a.gat.gw[j] * un[a.gat.idx[j]];
     }
@@ -325,6 +344,328 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
             ge = a.gat.cell_start[cbase + c1];
         }
         sparse_phase<ADJ>(a, ib, ie, gb, ge, so, tid, 32 * BZ);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D step, shot groups.  A CTA owns one 128 x TZ tile and runs it for G
+// consecutive shots of the batch (blockIdx.z = group).  Everything that does
+// not depend on the shot -- the model, the sponge factors and their
+// reciprocal -- is computed once per CTA; the next shot's halo tile is
+// prefetched with cp.async into the second of two shared-memory buffers while
+// the current shot is computed; in the adjoint the imaging condition is
+// accumulated over the group in a shared-memory tile and written back once,
+// into the group's gradient accumulator (buffer G holds one per group).
+template <int TZ, int BZ, int G, bool ADJ>
+__global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
+{
+    constexpr int SW = kTX + 8;
+    constexpr int RB = TZ / BZ;
+    extern __shared__ __align__(16) float dsm[];
+    float(*s)[TZ + 8][SW] = reinterpret_cast<float(*)[TZ + 8][SW]>(dsm);
+    float* sg = dsm + 2 * (TZ + 8) * SW;  // [TZ][kTX], adjoint only
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * kTX, z0 = blockIdx.y * TZ;
+    const int grp = blockIdx.z, s0 = grp * G, s1 = min(s0 + G, a.nshot);
+    const int lx = 4 * tx, gx = x0 + lx;
+    const int nvalid = min(4, a.Nx - gx);
+    const bool imaging = ADJ && a.gacc != nullptr;
+    const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
+
+    float4 kp[RB];
+    float eps[RB][4], inv[RB][4];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+        const int gz = z0 + ty + rr * BZ;
+        kp[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gz < a.Nz && nvalid > 0) kp[rr] = ld4(a.kap + (long long)gz * a.P + gx);
+        const int dz = sponge_depth(gz, a.nb, a.nz);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
+            eps[rr][e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
+            inv[rr][e] = __frcp_rn(1.0f + eps[rr][e]);
+        }
+    }
+    float* gq = imaging ? a.gacc + (long long)grp * a.cell : nullptr;
+    if (imaging) {
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ, gz = z0 + r;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gz < a.Nz && nvalid > 0) v = *reinterpret_cast<const float4*>(gq + (long long)gz * a.P + gx);
+            *reinterpret_cast<float4*>(sg + r * kTX + lx) = v;
+        }
+    }
+
+    auto load_tile = [&](int buf, int shot) {
+        const float* u = a.u + (long long)shot * a.cell;
+        for (int r = ty; r < TZ + 8; r += BZ) {
+            const int gz = z0 - 4 + r;
+            for (int c4 = tx; c4 < SW / 4; c4 += 32) {
+                const int gxx = x0 - 4 + 4 * c4;
+                const bool ok = gz >= 0 && gz < a.Nz && gxx >= 0 && gxx < a.P;
+                cp_async16(&s[buf][r][4 * c4], ok ? u + (long long)gz * a.P + gxx : a.u, ok ? 16 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+
+    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
+    load_tile(0, s0);
+    for (int shot = s0; shot < s1; ++shot) {
+        const int cur = (shot - s0) & 1;
+        if (shot + 1 < s1) load_tile(cur ^ 1, shot + 1);
+        else cp_async_commit();  // keep one group per iteration
+        const long long so = (long long)shot * a.cell;
+        float4 uo[RB];
+        float uf[RB][4];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int gz = z0 + ty + rr * BZ;
+            uo[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) uf[rr][e] = 0.f;
+            if (gz < a.Nz && nvalid > 0) {
+                const long long off = so + (long long)gz * a.P + gx;
+                uo[rr] = *reinterpret_cast<const float4*>(a.uprev + off);
+                if (imaging) {
+                    if (a.uf16) {
+                        unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + off), uf[rr]);
+                    } else {
+                        const float4 v = ld4(a.uf32 + off);
+                        uf[rr][0] = v.x;
+                        uf[rr][1] = v.y;
+                        uf[rr][2] = v.z;
+                        uf[rr][3] = v.w;
+                    }
+                }
+            }
+        }
+        cp_async_wait_prev();
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ;
+            const int gz = z0 + r;
+            if (gz >= a.Nz) continue;
+            if (nvalid <= 0) {
+                zero_padding(a, so, (long long)gz * a.P + gx, gx);
+                continue;
+            }
+            const float* row = &s[cur][r + 4][lx];
+            const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+            float lap[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
+                         kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
+#pragma unroll
+            for (int k = 1; k <= 4; ++k) {
+                const float4 U = lds4(&s[cur][r + 4 - k][lx + 4]);
+                const float4 D = lds4(&s[cur][r + 4 + k][lx + 4]);
+                lap[0] += ck[k] * (U.x + D.x);
+                lap[1] += ck[k] * (U.y + D.y);
+                lap[2] += ck[k] * (U.z + D.z);
+                lap[3] += ck[k] * (U.w + D.w);
+            }
+            float out[4], cen[4], um[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                cen[e] = w[e + 4];
+                um[e] = f4(uo[rr], e);
+                out[e] = fmaf(f4(kp[rr], e), lap[e], fmaf(eps[rr][e], um[e], 2.0f * cen[e] - um[e])) * inv[rr][e];
+            }
+            write4<ADJ>(a, so, (long long)gz * a.P + gx, nvalid, out, cen, um, false, nullptr,
+                        make_float4(0.f, 0.f, 0.f, 0.f));
+            if (imaging) {
+                float* g = sg + r * kTX + lx;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) g[e] -= uf[rr][e] * (out[e] - 2.0f * cen[e] + um[e]);
+            }
+        }
+        __syncthreads();
+        if (sparse) {
+            const int kcell = TZ / a.TZc;
+            const int cbase = (shot * a.ncx + (int)blockIdx.x) * a.ncz;
+            const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
+            int ib = 0, ie = 0, gb = 0, ge = 0;
+            if (a.inj.cell_start) {
+                ib = a.inj.cell_start[cbase + c0];
+                ie = a.inj.cell_start[cbase + c1];
+            }
+            if (a.gat.cell_start) {
+                gb = a.gat.cell_start[cbase + c0];
+                ge = a.gat.cell_start[cbase + c1];
+            }
+            sparse_phase<ADJ>(a, ib, ie, gb, ge, so, tid, 32 * BZ, imaging ? sg : nullptr, z0, x0);
+        }
+    }
+    if (imaging) {
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ, gz = z0 + r;
+            if (gz < a.Nz && nvalid > 0)
+                *reinterpret_cast<float4*>(gq + (long long)gz * a.P + gx) =
+                    *reinterpret_cast<const float4*>(sg + r * kTX + lx);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D step, z-march.  Each warp owns a 128-column strip of TZ consecutive rows
+// of one shot (a CTA stacks NW such warps in z) and walks down it: lane l
+// keeps the 9-row z window of its 4 columns in registers, takes its x
+// neighbours from lanes l-1 and l+1 by shuffles (lanes 0 and 31 load the
+// 4-column halo of the strip), and prefetches the previous level, the model
+// and, in the adjoint, the forward field and the gradient D rows ahead.  No
+// shared memory and no block barriers: warps stream independently.  Rows in
+// the interior of the grid skip the sponge factors.
+template <int TZ, int NW, int D, bool ADJ>
+__global__ void __launch_bounds__(32 * NW) k_step2d_zm(const StepArgs a)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * kTX;
+    const int zs = ((int)blockIdx.y * NW + warp) * TZ;
+    if (zs >= a.Nz) return;  // warp-uniform; no block barrier follows
+    const int ze = min(zs + TZ, a.Nz);
+    const int shot = blockIdx.z;
+    const long long so = (long long)shot * a.cell;
+    const float* __restrict__ u = a.u + so;
+    const int gx = x0 + 4 * lane;
+    const int nvalid = min(4, a.Nx - gx);
+    const bool in_p = gx < a.P;
+    const int hx = lane == 0 ? x0 - 4 : x0 + kTX;
+    const bool hok = (lane == 0 || lane == 31) && hx >= 0 && hx < a.P;
+    const bool imaging = ADJ && a.gacc != nullptr;
+    const bool xin = x0 >= a.nb && x0 + kTX - 1 <= a.nb + a.nx - 1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    auto ldu = [&](int z) { return (z >= 0 && z < a.Nz && in_p) ? ld4(u + (long long)z * a.P + gx) : z4; };
+    auto ldh = [&](int z) { return (hok && z < ze) ? ld4(u + (long long)z * a.P + hx) : z4; };
+    auto ldp = [&](int z) {
+        return (z < ze && nvalid > 0) ? *reinterpret_cast<const float4*>(a.uprev + so + (long long)z * a.P + gx) : z4;
+    };
+    auto ldk = [&](int z) { return (z < ze && nvalid > 0) ? ld4(a.kap + (long long)z * a.P + gx) : z4; };
+    auto ldf = [&](int z) {
+        if (!imaging || z >= ze || nvalid <= 0) return z4;
+        const long long off = so + (long long)z * a.P + gx;
+        if (a.uf16) {
+            float t[4];
+            unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + off), t);
+            return make_float4(t[0], t[1], t[2], t[3]);
+        }
+        return ld4(a.uf32 + off);
+    };
+    auto ldg = [&](int z) {
+        return (imaging && z < ze && nvalid > 0)
+                   ? *reinterpret_cast<const float4*>(a.gacc + so + (long long)z * a.P + gx)
+                   : z4;
+    };
+
+    float4 q[9];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = ldu(zs - 4 + k);
+    float4 hq[D], pq[D], kq[D], fq[D], gq[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        hq[d] = ldh(zs + d);
+        pq[d] = ldp(zs + d);
+        kq[d] = ldk(zs + d);
+        fq[d] = ldf(zs + d);
+        gq[d] = ldg(zs + d);
+    }
+    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
+    for (int z = zs; z < ze; ++z) {
+        q[8] = ldu(z + 4);
+        const float4 hc = hq[0], pc = pq[0], kc = kq[0], fc = fq[0], gc = gq[0];
+#pragma unroll
+        for (int d = 0; d + 1 < D; ++d) {
+            hq[d] = hq[d + 1];
+            pq[d] = pq[d + 1];
+            kq[d] = kq[d + 1];
+            fq[d] = fq[d + 1];
+            gq[d] = gq[d + 1];
+        }
+        hq[D - 1] = ldh(z + D);
+        pq[D - 1] = ldp(z + D);
+        kq[D - 1] = ldk(z + D);
+        fq[D - 1] = ldf(z + D);
+        gq[D - 1] = ldg(z + D);
+
+        const float4 B = q[4];
+        float4 A, C;
+        A.x = __shfl_up_sync(FULL, B.x, 1);
+        A.y = __shfl_up_sync(FULL, B.y, 1);
+        A.z = __shfl_up_sync(FULL, B.z, 1);
+        A.w = __shfl_up_sync(FULL, B.w, 1);
+        C.x = __shfl_down_sync(FULL, B.x, 1);
+        C.y = __shfl_down_sync(FULL, B.y, 1);
+        C.z = __shfl_down_sync(FULL, B.z, 1);
+        C.w = __shfl_down_sync(FULL, B.w, 1);
+        if (lane == 0) A = hc;
+        if (lane == 31) C = hc;
+        const long long off = (long long)z * a.P + gx;
+        if (nvalid > 0) {
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+            float lap[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
+                         kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
+#pragma unroll
+            for (int k = 1; k <= 4; ++k) {
+                lap[0] += ck[k] * (q[4 - k].x + q[4 + k].x);
+                lap[1] += ck[k] * (q[4 - k].y + q[4 + k].y);
+                lap[2] += ck[k] * (q[4 - k].z + q[4 + k].z);
+                lap[3] += ck[k] * (q[4 - k].w + q[4 + k].w);
+            }
+            float out[4], cen[4], um[4];
+            const bool interior = xin && z >= a.nb && z <= a.nb + a.nz - 1;
+            if (interior) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    cen[e] = w[e + 4];
+                    um[e] = f4(pc, e);
+                    out[e] = fmaf(f4(kc, e), lap[e], 2.0f * cen[e] - um[e]);
+                }
+            } else {
+                const int dz = sponge_depth(z, a.nb, a.nz);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
+                    const float kap = f4(kc, e);
+                    const float eps = kap * a.ceps * (float)(dd * dd);
+                    cen[e] = w[e + 4];
+                    um[e] = f4(pc, e);
+                    out[e] = leap(cen[e], um[e], lap[e], kap, eps);
+                }
+            }
+            const float uf[4] = {fc.x, fc.y, fc.z, fc.w};
+            write4<ADJ>(a, so, off, nvalid, out, cen, um, imaging, uf, gc);
+        } else if (in_p) {
+            zero_padding(a, so, off, gx);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+    }
+    if (a.inj.cell_start || a.gat.cell_start) {
+        __syncwarp();
+        const int cbase = (shot * a.ncx + (int)blockIdx.x) * a.ncz;
+        const int c0 = zs / a.TZc, c1 = min(c0 + TZ / a.TZc, a.ncz);
+        int ib = 0, ie = 0, gb = 0, ge = 0;
+        if (a.inj.cell_start) {
+            ib = a.inj.cell_start[cbase + c0];
+            ie = a.inj.cell_start[cbase + c1];
+        }
+        if (a.gat.cell_start) {
+            gb = a.gat.cell_start[cbase + c0];
+            ge = a.gat.cell_start[cbase + c1];
+        }
+        sparse_phase<ADJ, true>(a, ib, ie, gb, ge, so, lane, 32);
     }
 }
 
@@ -656,17 +997,27 @@ static void launch_2d(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 
 // 2D variants (which = 0 forward, 1 adjoint).  The TMA map boxes and the
 // launch below must agree on TZ; plan/api read TZ from this table.
-static const Variant2D kFwd2D[] = {{0, 32, 4, 0}, {1, 48, 6, 2}, {1, 32, 4, 3}, {1, 24, 3, 4}, {1, 16, 2, 4},
-                                   {1, 32, 2, 3}};
-static const Variant2D kAdj2D[] = {{0, 32, 4, 0}, {1, 24, 3, 3}, {1, 16, 2, 4}, {1, 32, 4, 2}};
+static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4, 3, 0}, {1, 24, 3, 4, 0},
+                                   {1, 16, 2, 4, 0}, {1, 32, 2, 3, 0}, {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4},
+                                   {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2}, {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0},
+                                   {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0}, {1, 32, 1, 3, 0}, {2, 16, 8, 0, 8},
+                                   {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}};
+static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
+                                   {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
+                                   {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
+                                   {1, 16, 1, 4, 0}, {2, 16, 8, 0, 8}, {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}};
 static int g_selected[2] = {-1, -1};
-static const int kDefault2D[2] = {0, 0};
+static const int kDefault2D[2] = {9, 7};
 
-int variant_count(int which) { return which == 0 ? 6 : (which == 1 ? 4 : 0); }
+int variant_count(int which)
+{
+    return which == 0 ? (int)(sizeof(kFwd2D) / sizeof(kFwd2D[0]))
+                      : (which == 1 ? (int)(sizeof(kAdj2D) / sizeof(kAdj2D[0])) : 0);
+}
 
 Variant2D variant_info(int which, int v)
 {
-    if (v < 0 || v >= variant_count(which)) return Variant2D{-1, 0, 0, 0};
+    if (v < 0 || v >= variant_count(which)) return Variant2D{-1, 0, 0, 0, 0};
     return which == 0 ? kFwd2D[v] : kAdj2D[v];
 }
 
@@ -676,11 +1027,33 @@ int current_variant(int which)
     return g_selected[which] >= 0 ? g_selected[which] : kDefault2D[which];
 }
 
+bool variant_forced(int which) { return which >= 0 && which <= 1 && g_selected[which] >= 0; }
+
 int select_variant(int which, int v)
 {
     if (which < 0 || which > 1 || v < -1 || v >= variant_count(which)) return -1;
     g_selected[which] = v;
     return 0;
+}
+
+template <int TZ, int BZ, int G, bool ADJ>
+static void launch_2d_group(const StepArgs& a, cudaStream_t s)
+{
+    constexpr size_t smem = (size_t)(2 * (TZ + 8) * (kTX + 8) + (ADJ ? TZ * kTX : 0)) * 4;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_step2d_sg<TZ, BZ, G, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
+    k_step2d_sg<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(a);
+}
+
+template <int TZ, int NW, int D, bool ADJ>
+static void launch_2d_march(const StepArgs& a, cudaStream_t s)
+{
+    dim3 grid(a.ncx, (a.Nz + TZ * NW - 1) / (TZ * NW), a.nshot);
+    k_step2d_zm<TZ, NW, D, ADJ><<<grid, 32 * NW, 0, s>>>(a);
 }
 
 template <int TZ, int BZ, bool ADJ>
@@ -701,6 +1074,18 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 3: launch_2d<24, 3, 4, false>(a, maps, s); break;
             case 4: launch_2d<16, 2, 4, false>(a, maps, s); break;
             case 5: launch_2d<32, 2, 3, false>(a, maps, s); break;
+            case 6: launch_2d_group<32, 8, 4, false>(a, s); break;
+            case 7: launch_2d_group<16, 8, 4, false>(a, s); break;
+            case 8: launch_2d_group<32, 8, 8, false>(a, s); break;
+            case 9: launch_2d_group<16, 8, 2, false>(a, s); break;
+            case 10: launch_2d_march<24, 4, 1, false>(a, s); break;
+            case 11: launch_2d_march<24, 4, 2, false>(a, s); break;
+            case 12: launch_2d_march<48, 4, 2, false>(a, s); break;
+            case 13: launch_2d_march<16, 8, 2, false>(a, s); break;
+            case 14: launch_2d<32, 1, 3, false>(a, maps, s); break;
+            case 15: launch_2d_group<16, 8, 8, false>(a, s); break;
+            case 16: launch_2d_group<16, 8, 16, false>(a, s); break;
+            case 17: launch_2d_group<8, 8, 8, false>(a, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -708,6 +1093,18 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 1: launch_2d<24, 3, 3, true>(a, maps, s); break;
             case 2: launch_2d<16, 2, 4, true>(a, maps, s); break;
             case 3: launch_2d<32, 4, 2, true>(a, maps, s); break;
+            case 4: launch_2d_group<32, 8, 4, true>(a, s); break;
+            case 5: launch_2d_group<16, 8, 4, true>(a, s); break;
+            case 6: launch_2d_group<32, 8, 8, true>(a, s); break;
+            case 7: launch_2d_group<16, 8, 2, true>(a, s); break;
+            case 8: launch_2d_march<24, 4, 1, true>(a, s); break;
+            case 9: launch_2d_march<24, 4, 2, true>(a, s); break;
+            case 10: launch_2d_march<48, 4, 2, true>(a, s); break;
+            case 11: launch_2d_march<16, 8, 2, true>(a, s); break;
+            case 12: launch_2d<16, 1, 4, true>(a, maps, s); break;
+            case 13: launch_2d_group<16, 8, 8, true>(a, s); break;
+            case 14: launch_2d_group<16, 8, 16, true>(a, s); break;
+            case 15: launch_2d_group<8, 8, 8, true>(a, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "internal.h"
 
@@ -31,7 +32,19 @@ Dims make_dims(const wave_grid_t& g)
     return d;
 }
 
-Tiling choose_tiling(const Dims& d)
+// Variants picked by wave_autotune, per (padded grid, shot count).
+namespace {
+std::mutex g_tuned_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
+}  // namespace
+
+void remember_tuning(const Dims& d, int nshot, int vf, int va)
+{
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    g_tuned[std::make_tuple(d.Nx, d.Nz, nshot)] = std::make_pair(vf, va);
+}
+
+Tiling choose_tiling(const Dims& d, int nshot)
 {
     Tiling t;
     t.TX = kTX;
@@ -41,6 +54,13 @@ Tiling choose_tiling(const Dims& d)
         t.TZc = kTZc2;
         t.vf = current_variant(0);
         t.va = current_variant(1);
+        // an explicit wave_set_variant wins over a tuned choice
+        std::lock_guard<std::mutex> lock(g_tuned_mu);
+        auto it = g_tuned.find(std::make_tuple(d.Nx, d.Nz, nshot));
+        if (it != g_tuned.end()) {
+            if (!variant_forced(0)) t.vf = it->second.first;
+            if (!variant_forced(1)) t.va = it->second.second;
+        }
     } else {
         t.TY = 8;
         t.TZc = 32;
@@ -49,6 +69,13 @@ Tiling choose_tiling(const Dims& d)
     t.ncy = (d.Ny + t.TY - 1) / t.TY;
     t.ncz = (d.Nz + t.TZc - 1) / t.TZc;
     return t;
+}
+
+int gradient_accumulators(const Tiling& t, int ndim, int nshot)
+{
+    if (ndim != 2) return nshot;
+    const Variant2D v = variant_info(1, t.va);
+    return v.kind == 2 ? (nshot + v.G - 1) / v.G : nshot;
 }
 
 // Interpolation taps of one point: bilinear (2D) / trilinear (3D) weights on

@@ -79,6 +79,9 @@ def _lib():
         lib.wave_status_str.restype = ctypes.c_char_p
         lib.wave_forward_static.argtypes = [G, P, I, I, P, P, I, P, P, P]
         lib.wave_forward_static.restype = I
+        lib.wave_autotune.argtypes = [G, P, I, I, P, P, I, P, I, P, ctypes.c_size_t, P,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        lib.wave_autotune.restype = I
         lib.wave_set_variant.argtypes = [I, I]
         lib.wave_set_variant.restype = I
         lib.wave_variant_count.argtypes = [I]
@@ -324,3 +327,23 @@ def wave_set_variant(which: int, variant: int) -> None:
 
 def wave_variant_count(which: int) -> int:
     return int(_lib().wave_variant_count(int(which)))
+
+
+def wave_autotune(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, steps: int = 20,
+                  stream=None):
+    """Times every 2D step variant on this problem and remembers the fastest
+    for this grid and shot count; returns (forward variant, adjoint variant)."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pw = _dev(wavelet, "wavelet", (ns, grid.nt, nsrc))
+    nbytes = wave_workspace_size(grid, OP_GRADIENT, src, rec, STORE_CHECKPOINT, 1)
+    work = _workspace(nbytes, vel.device)
+    bf, ba = ctypes.c_int(-1), ctypes.c_int(-1)
+    g = grid.c()
+    st = _lib().wave_autotune(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), int(steps),
+                              work.data_ptr(), work.numel(), _stream(stream), ctypes.byref(bf), ctypes.byref(ba))
+    if st:
+        raise WaveError(st, "wave_autotune")
+    return bf.value, ba.value

@@ -212,9 +212,9 @@ def restore_variants():
 
 
 def test_every_2d_kernel_variant_matches(restore_variants):
-    """Each 2D step variant (direct loads, TMA pipelines of several tile heights
-    and depths) gives the oracle's records and gradient, and the same bits as
-    variant 0 (the per-point arithmetic does not depend on the tiling)."""
+    """Each 2D step variant gives the oracle's records and gradient; records
+    are bitwise those of variant 0 (the per-point arithmetic does not depend on
+    the tiling) and gradients agree to rounding (the shot sum may be grouped)."""
     p = synth.small_2d(91, nx=150, nz=61, nt=240, nshot=3, nrec=41)
     q, v0, dobs = _grad_case(p)
     g = Grid.of(p)
@@ -234,4 +234,20 @@ def test_every_2d_kernel_variant_matches(restore_variants):
             if base is None:
                 base = (d, gr)
             else:
-                assert torch.equal(d, base[0]) and torch.equal(gr, base[1]), (vf, va)
+                # records are bitwise the same; shot-group kernels sum the
+                # gradient per group first, so only the summation order differs
+                assert torch.equal(d, base[0]), (vf, va)
+                assert float((gr - base[1]).norm() / base[1].norm()) < 1e-5, (vf, va)
+
+
+def test_autotune_picks_valid_variants_and_results_hold(restore_variants):
+    p = synth.small_2d(92, nx=120, nz=50, nt=200, nshot=4, nrec=30)
+    q, v0, dobs = _grad_case(p)
+    g = Grid.of(p)
+    bf, ba = wave.wave_autotune(g, dev(v0), p.src, dev(q), p.rec, steps=5)
+    assert 0 <= bf < wave.wave_variant_count(0) and 0 <= ba < wave.wave_variant_count(1)
+    _, gr, _ = wave.wave_gradient(g, dev(v0), p.src, dev(q), p.rec, dev(dobs), nsnap=9)
+    _, g_ref = oracle.gradient(ogrid(p), v0, p.src, q, p.rec, dobs)
+    assert rel(gr.cpu().numpy(), g_ref) < TOL_GRAD
+    p3 = synth.small_3d(93, nt=40)
+    assert wave.wave_autotune(Grid.of(p3), dev(p3.vel), p3.src, dev(ricker_batch(p3)), p3.rec, steps=3) == (-1, -1)
