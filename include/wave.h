@@ -79,8 +79,9 @@ typedef enum {
     WAVE_STORE_FP32 = 2        /* every u^n stored in FP32 (exact, most memory)    */
 } wave_store_t;
 
-/* Bytes of device workspace that wave_forward (op 0), wave_adjoint (op 1) or
- * wave_gradient (op 2) needs for this problem.  The coordinates (host, same
+/* Bytes of device workspace that wave_forward (op 0), wave_adjoint (op 1),
+ * wave_gradient / wave_jacobian_adjoint (op 2) or wave_born (op 3) needs for
+ * this problem.  The coordinates (host, same
  * layout as in the calls) are needed because interpolation taps of zero
  * weight are dropped.  `store` and `nsnap` matter for op 2 only (nsnap =
  * number of checkpoint slots, each holding two FP32 wavefields per shot; the
@@ -109,6 +110,12 @@ wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot,
                            const float* src_xyz, int nrec, const float* rec_xyz, const float* resid,
                            float* src_out, void* work, size_t work_bytes, void* stream);
 
+/* Parameter the gradients are taken with respect to. */
+typedef enum {
+    WAVE_WRT_SLOWNESS2 = 0, /* dPhi/dm, m = 1/v^2 (the paper's parameter) */
+    WAVE_WRT_VELOCITY = 1   /* dPhi/dv = -2 / v^3 dPhi/dm                  */
+} wave_wrt_t;
+
 /* FWI gradient (judiJacobian(F, q)' * (F q - d), i.e. J' applied to the data
  * residual) of Phi(m) = 1/2 sum_s ||F_s(m) q_s - d_s||^2 with respect to the
  * physical squared slowness m = 1/v^2, summed over shots:
@@ -120,11 +127,34 @@ wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot,
  *   grad     dev  out [nz][(ny)][nx] dPhi/dm
  *   d_syn    dev  out [nshot][nt][nrec] synthetic data, or NULL
  *   misfit   host out Phi (double), or NULL
- *   store    a wave_store_t; nsnap = checkpoint slots (CHECKPOINT only, >= 1) */
+ *   store    a wave_store_t; nsnap = checkpoint slots (CHECKPOINT only, >= 1)
+ *   wrt      a wave_wrt_t: gradient w.r.t. m (default) or w.r.t. v */
 wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
                             const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
                             const float* d_obs, float* grad, float* d_syn, double* misfit, int store,
-                            int nsnap, void* work, size_t work_bytes, void* stream);
+                            int nsnap, int wrt, void* work, size_t work_bytes, void* stream);
+
+/* Adjoint of the Jacobian applied to an arbitrary data-space vector r,
+ * summed over shots: J(m)' r with J the Jacobian of d = F(m) q (the first
+ * output of the pullback of the rrule for F*q, judiJacobian(F, q)' * dy).
+ * Same arguments as wave_gradient, with the residual r (dev [nshot][nt][nrec])
+ * in place of d_obs and no synthetic data or misfit.  Workspace: op 2. */
+wave_status_t wave_jacobian_adjoint(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
+                                    const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
+                                    const float* resid, float* grad, int store, int nsnap, int wrt, void* work,
+                                    size_t work_bytes, void* stream);
+
+/* Born modelling, the Jacobian applied to a model perturbation:
+ * d = J(m) dm (judiJacobian(F, q) * dm), linearised about m = 1/vel^2:
+ *   (M+E) du^{n+1} = (2M + dt^2 L) du^n - (M-E) du^{n-1}
+ *                    - Extend(dm) .* (u^{n+1} - 2 u^n + u^{n-1}),  d^n = R du^n,
+ * u the background field of wave_forward.
+ *   dm    dev [nz][(ny)][nx] perturbation of the squared slowness
+ *   data  dev out [nshot][nt][nrec]
+ * Workspace: op 3 of wave_workspace_size. */
+wave_status_t wave_born(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                        const float* wavelet, int nrec, const float* rec_xyz, const float* dm, float* data,
+                        void* work, size_t work_bytes, void* stream);
 
 /* Forward modelling without a caller workspace, for callers that cannot
  * allocate device memory when they model: e.g. a plugin whose host

@@ -1,0 +1,43 @@
+"""Differentiable wave modelling for PyTorch (the AD rule of the paper's
+section "Wave-equation-based inversion": the pullback of d = F(m) q returns
+J' dy with respect to the model and F' dy with respect to the source).
+
+``ForwardModel.apply(vel, wavelet, grid, src_xyz, rec_xyz)`` returns the shot
+records; its backward calls libwave's ``wave_jacobian_adjoint`` (checkpointed
+or BF16-store adjoint-state gradient, with the chain rule to velocity applied
+in the library) and ``wave_adjoint``.  No arithmetic of the method happens in
+Python.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import wave
+
+
+class ForwardModel(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vel, wavelet, grid, src_xyz, rec_xyz, store=wave.STORE_CHECKPOINT, nsnap=64):
+        vel = vel.contiguous()
+        wavelet = wavelet.contiguous()
+        ctx.save_for_backward(vel, wavelet)
+        ctx.meta = (grid, src_xyz, rec_xyz, store, nsnap)
+        return wave.wave_forward(grid, vel, src_xyz, wavelet, rec_xyz)
+
+    @staticmethod
+    def backward(ctx, dy):
+        vel, wavelet = ctx.saved_tensors
+        grid, src, rec, store, nsnap = ctx.meta
+        dy = dy.contiguous()
+        g_vel = g_wav = None
+        if ctx.needs_input_grad[0]:
+            g_vel = wave.wave_jacobian_adjoint(grid, vel, src, wavelet, rec, dy, store=store, nsnap=nsnap,
+                                               wrt=wave.WRT_VELOCITY)
+        if ctx.needs_input_grad[1]:
+            g_wav = wave.wave_adjoint(grid, vel, src, rec, dy)
+        return g_vel, g_wav, None, None, None, None, None
+
+
+def forward_model(vel, wavelet, grid, src_xyz, rec_xyz, store=wave.STORE_CHECKPOINT, nsnap=64):
+    """Shot records with autograd support for vel and wavelet."""
+    return ForwardModel.apply(vel, wavelet, grid, src_xyz, rec_xyz, store, nsnap)

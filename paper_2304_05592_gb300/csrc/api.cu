@@ -42,6 +42,7 @@ struct DevTaps {
 //   forward  : W0 W1
 //   adjoint  : A0 A1
 //   gradient : W0 W1 A0 A1 G Z S(0).cur S(0).prev ... [FP32 store rows 0..nt-1]
+//   Born     : W0 W1 W2 (background levels) A0 A1 (scattered levels)
 // W = forward levels, A = adjoint levels, G = per-shot gradient accumulators,
 // Z = a zero batch (the state before the first step), S(k) = checkpoint slot k.
 struct Layout {
@@ -61,6 +62,7 @@ struct Layout {
     float* slots_rec = nullptr;
     float* slots_src = nullptr;
     float* dsyn = nullptr;
+    float* dmv = nullptr;
     __nv_bfloat16* st16 = nullptr;
     size_t bytes = 0;
     StepMaps maps;
@@ -120,7 +122,7 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
 {
     wave_status_t st = check_grid(g);
     if (st) return st;
-    if (op < 0 || op > 2 || nshot < 0 || nsrc < 0 || nrec < 0) return WAVE_ERR_ARG;
+    if (op < 0 || op > 3 || nshot < 0 || nsrc < 0 || nrec < 0) return WAVE_ERR_ARG;
     if ((nshot && nsrc && !src_xyz) || (nshot && nrec && !rec_xyz)) return WAVE_ERR_ARG;
     if (op == 2 && (store < 0 || store > 2 || (store == WAVE_STORE_CHECKPOINT && nsnap < 1))) return WAVE_ERR_ARG;
     if ((long long)nshot * g->nt * std::max(nsrc, nrec) >= (1LL << 31)) return WAVE_ERR_ARG;
@@ -145,6 +147,10 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
     } else if (op == 1) {
         L.iA0 = 0;
         L.nbuf = 2;
+    } else if (op == 3) {
+        L.iW0 = 0;  // three background levels W0 W1 W2, then the scattered field A0 A1
+        L.iA0 = 3;
+        L.nbuf = 5;
     } else {
         L.iW0 = 0;
         L.iA0 = 2;
@@ -167,7 +173,8 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
     carve_taps(c, L.hs, ncells_all, L.ts);
     carve_taps(c, L.hr, ncells_all, L.tr);
     L.pool = c.take<float>((size_t)L.nbuf * L.field());
-    if (op == 0 || op == 2) L.slots_rec = c.take<float>(nt * L.hr.idx.size());
+    if (op == 0 || op == 2 || op == 3) L.slots_rec = c.take<float>(nt * L.hr.idx.size());
+    if (op == 3) L.dmv = c.take<float>(d.cell);
     if (op == 1) L.slots_src = c.take<float>(nt * L.hs.idx.size());
     if (op == 2) {
         L.dsyn = c.take<float>((size_t)nshot * nt * nrec);
@@ -430,8 +437,8 @@ wave_status_t check_work(const Layout& L, void* work, size_t work_bytes)
 // only renames which buffers hold (u^j, u^{j-1}), the last two steps of an
 // advance that ends in a save write straight into the slot, and a step that
 // starts from a slot writes out of place into W0/W1.
-wave_status_t run_checkpointed(Layout& L, const float* wavelet, const float* d_obs,
-                               const std::function<void()>& finalize_data, cudaStream_t s)
+wave_status_t run_checkpointed(Layout& L, const float* wavelet, const float* amp_a, const float* amp_b,
+                               bool record_data, const std::function<void()>& finalize_data, cudaStream_t s)
 {
     const Dims& d = L.d;
     const Schedule sch = make_schedule(d.nt, L.nsnap);
@@ -454,7 +461,7 @@ wave_status_t run_checkpointed(Layout& L, const float* wavelet, const float* d_o
                 else if (to_slot && n == j1 - 2) out = slot_prev(slot);
                 else if (prev == W0 || prev == W1) out = prev;
                 else out = cur == W0 ? W1 : W0;
-                const bool rec = n >= recorded;
+                const bool rec = record_data && n >= recorded;
                 fwd_step(L, cur, prev, out, n, wavelet, rec, nullptr, nullptr, s);
                 if (rec) recorded = n + 1;
                 prev = cur;
@@ -482,16 +489,16 @@ wave_status_t run_checkpointed(Layout& L, const float* wavelet, const float* d_o
             state = sch.state_of(act.b);
             break;
         case kFinalize:
-            if (recorded != sch.K) return WAVE_ERR_ARG;  // not reachable
+            if (record_data && recorded != sch.K) return WAVE_ERR_ARG;  // not reachable
             finalize_data();
             break;
         case kAdjointPair: {
             const int j = sch.state_of(act.a);
             if (j != state) return WAVE_ERR_ARG;  // not reachable
-            adj_step(L, A0 + acur, A0 + 1 - acur, j, L.dsyn, d_obs, false, cur, -1, s);
+            adj_step(L, A0 + acur, A0 + 1 - acur, j, amp_a, amp_b, false, cur, -1, s);
             acur ^= 1;
             if (j - 1 >= 1) {
-                adj_step(L, A0 + acur, A0 + 1 - acur, j - 1, L.dsyn, d_obs, false, prev, -1, s);
+                adj_step(L, A0 + acur, A0 + 1 - acur, j - 1, amp_a, amp_b, false, prev, -1, s);
                 acur ^= 1;
             }
             break;
@@ -589,16 +596,24 @@ wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot,
     return finish(L, s);
 }
 
-wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
-                            const float* wavelet, int nrec, const float* rec_xyz, const float* d_obs, float* grad,
-                            float* d_syn, double* misfit, int store, int nsnap, void* work, size_t work_bytes,
-                            void* stream)
+}  // extern "C"
+
+namespace {
+
+// J' applied to a data-space vector, summed over shots: the residual is either
+// given (resid) or formed on the fly as d_syn - d_obs (then the synthetic data
+// and the misfit are produced as well).
+wave_status_t gradient_impl(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                            const float* wavelet, int nrec, const float* rec_xyz, const float* d_obs,
+                            const float* resid, float* grad, float* d_syn, double* misfit, int store, int nsnap,
+                            int wrt, void* work, size_t work_bytes, cudaStream_t s)
 {
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     Layout L;
     wave_status_t st = plan(grid, 2, nshot, nsrc, src_xyz, nrec, rec_xyz, store, nsnap, work, L);
     if (st) return st;
-    if (!vel || !grad || (nshot && nsrc && !wavelet) || (nshot && nrec && !d_obs)) return WAVE_ERR_ARG;
+    if (wrt != WAVE_WRT_SLOWNESS2 && wrt != WAVE_WRT_VELOCITY) return WAVE_ERR_ARG;
+    const bool given = resid != nullptr;
+    if (!vel || !grad || (nshot && nsrc && !wavelet) || (nshot && nrec && !given && !d_obs)) return WAVE_ERR_ARG;
     if ((st = check_work(L, work, work_bytes))) return st;
     const Dims& d = L.d;
     if (nshot == 0) {
@@ -613,11 +628,14 @@ wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot
     // W0 W1 A0 A1 G Z are contiguous: clear them in one go.
     CK(cudaMemsetAsync(L.buf(0), 0, 6 * fb, s));
     const size_t nrow = L.hr.idx.size();
-    if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
+    if (nrow && !given) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
     const long long ndata = (long long)nshot * d.nt * nrec;
     const int K = d.nt - 1;
+    const float* amp_a = given ? resid : L.dsyn;
+    const float* amp_b = given ? nullptr : d_obs;
 
     auto finalize_data = [&]() {
+        if (given) return;
         if (nrec) {
             launch_finalize(L.tr.l, L.slots_rec, nshot, d.nt, L.dsyn, s);
             launch_misfit(L.dsyn, d_obs, ndata, L.part, kNumPartials, L.misfit, s);
@@ -634,31 +652,109 @@ wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot
         for (int n = 0; n < K; ++n) {
             __nv_bfloat16* r16 = L.st16 ? L.st16 + (size_t)(n + 1) * field : nullptr;
             float* r32 = L.iT0 >= 0 ? L.buf(L.iT0 + n + 1) : nullptr;
-            fwd_step(L, W0 + cur, W0 + 1 - cur, W0 + 1 - cur, n, wavelet, true, r16, r32, s);
+            fwd_step(L, W0 + cur, W0 + 1 - cur, W0 + 1 - cur, n, wavelet, !given, r16, r32, s);
             cur ^= 1;
         }
         finalize_data();
         int acur = 0;
         for (int k = K; k >= 1; --k) {
-            if (L.st16) adj_step(L, A0 + acur, A0 + 1 - acur, k, L.dsyn, d_obs, false, -1, k, s);
-            else adj_step(L, A0 + acur, A0 + 1 - acur, k, L.dsyn, d_obs, false, L.iT0 + k, -1, s);
+            if (L.st16) adj_step(L, A0 + acur, A0 + 1 - acur, k, amp_a, amp_b, false, -1, k, s);
+            else adj_step(L, A0 + acur, A0 + 1 - acur, k, amp_a, amp_b, false, L.iT0 + k, -1, s);
             acur ^= 1;
         }
     } else if (K < 1) {
         finalize_data();
     } else {
-        st = run_checkpointed(L, wavelet, d_obs, finalize_data, s);
+        st = run_checkpointed(L, wavelet, amp_a, amp_b, !given, finalize_data, s);
         if (st) return st;
     }
     // A0 and A1 (contiguous) are free now: scratch for the reduction.
-    launch_grad_reduce(d, L.buf(L.iG), gradient_accumulators(L.t, d.ndim, nshot), L.buf(A0), grad, s);
+    launch_grad_reduce(d, L.buf(L.iG), gradient_accumulators(L.t, d.ndim, nshot), L.buf(A0), grad,
+                       wrt == WAVE_WRT_VELOCITY ? vel : nullptr, s);
     launch_nan_scan(grad, d.phys, L.err, s);
-    if (d_syn && ndata) CK(cudaMemcpyAsync(d_syn, L.dsyn, ndata * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (!given && d_syn && ndata)
+        CK(cudaMemcpyAsync(d_syn, L.dsyn, ndata * sizeof(float), cudaMemcpyDeviceToDevice, s));
     double hm = 0.0;
-    CK(cudaMemcpyAsync(&hm, L.misfit, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!given) CK(cudaMemcpyAsync(&hm, L.misfit, sizeof(double), cudaMemcpyDeviceToHost, s));
     st = finish(L, s);
-    if (st == WAVE_OK && misfit) *misfit = hm;
+    if (st == WAVE_OK && misfit) *misfit = given ? 0.0 : hm;
     return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                            const float* wavelet, int nrec, const float* rec_xyz, const float* d_obs, float* grad,
+                            float* d_syn, double* misfit, int store, int nsnap, int wrt, void* work,
+                            size_t work_bytes, void* stream)
+{
+    return gradient_impl(grid, vel, nshot, nsrc, src_xyz, wavelet, nrec, rec_xyz, d_obs, nullptr, grad, d_syn,
+                         misfit, store, nsnap, wrt, work, work_bytes, static_cast<cudaStream_t>(stream));
+}
+
+wave_status_t wave_jacobian_adjoint(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
+                                    const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
+                                    const float* resid, float* grad, int store, int nsnap, int wrt, void* work,
+                                    size_t work_bytes, void* stream)
+{
+    if (nshot && nrec && !resid) return WAVE_ERR_ARG;
+    static const float kNone = 0.0f;
+    return gradient_impl(grid, vel, nshot, nsrc, src_xyz, wavelet, nrec, rec_xyz, nullptr, resid ? resid : &kNone,
+                         grad, nullptr, nullptr, store, nsnap, wrt, work, work_bytes,
+                         static_cast<cudaStream_t>(stream));
+}
+
+wave_status_t wave_born(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
+                        const float* wavelet, int nrec, const float* rec_xyz, const float* dm, float* data, void* work,
+                        size_t work_bytes, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    wave_status_t st = plan(grid, 3, nshot, nsrc, src_xyz, nrec, rec_xyz, 0, 0, work, L);
+    if (st) return st;
+    if (nshot == 0) return WAVE_OK;
+    if (!vel || !dm || (nsrc && !wavelet) || (nrec && !data)) return WAVE_ERR_ARG;
+    if ((st = check_work(L, work, work_bytes))) return st;
+    L.t.vf = 0;  // the direct 2D kernel carries the scattering source
+    if ((st = setup(L, vel, s))) return st;
+    launch_prep_dm(L.d, dm, L.kap, L.dmv, s);
+    const size_t fb = L.field() * sizeof(float);
+    CK(cudaMemsetAsync(L.buf(0), 0, 5 * fb, s));
+    const size_t nrow = L.hr.idx.size();
+    if (nrow) CK(cudaMemsetAsync(L.slots_rec, 0, nrow * sizeof(float), s));
+    int cur = 0, prev = 1, nxt = 2;  // background u^n, u^{n-1}, free
+    int dcur = L.iA0, dprev = L.iA0 + 1;
+    for (int n = 0; n + 1 < L.d.nt; ++n) {
+        fwd_step(L, cur, prev, nxt, n, wavelet, false, nullptr, nullptr, s);  // u^{n+1}
+        StepArgs a = base_args(L);
+        a.u = L.buf(dcur);
+        a.uprev = L.buf(dprev);
+        a.unew = L.buf(dprev);
+        a.u_buf = dcur;
+        a.prev_buf = dprev;
+        a.dmv = L.dmv;
+        a.bs_a = L.buf(nxt);
+        a.bs_b = L.buf(cur);
+        a.bs_c = L.buf(prev);
+        if (nrec > 0 && L.tr.l.ntap > 0) {
+            a.gat = L.tr.l;
+            a.slots = L.slots_rec;
+            a.slot_row = n + 1;
+        }
+        launch_step(L.t, L.d.ndim, false, a, &L.maps, s);
+        const int t = prev;
+        prev = cur;
+        cur = nxt;
+        nxt = t;
+        std::swap(dcur, dprev);
+    }
+    if (nrec) {
+        launch_finalize(L.tr.l, L.slots_rec, nshot, L.d.nt, data, s);
+        launch_nan_scan(data, (long long)nshot * L.d.nt * nrec, L.err, s);
+    }
+    return finish(L, s);
 }
 
 wave_status_t wave_ricker(float f0, float dt, int nt, float* out, void* stream)

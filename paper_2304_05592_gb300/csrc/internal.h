@@ -114,6 +114,10 @@ struct StepArgs {
     const float* uf32;
     float* gacc;         // [nshot][cell]
     int* err;
+    // Born scattering source: unew gets -dmv .* (bs_a - 2 bs_b + bs_c) / (1 + eps)
+    // added, dmv = Extend(dm) v^2 (kind 0 2D kernel and the 3D kernel only)
+    const float* dmv;
+    const float *bs_a, *bs_b, *bs_c;
     // pool indices of the same buffers for the TMA kernels (-1: none)
     int u_buf, prev_buf, uf_buf, g_buf, uf16_row;
 };
@@ -126,8 +130,10 @@ void launch_tapfac(const Dims& d, const TapList& l, const float* kap, float scal
 void launch_finalize(const TapList& l, const float* slots, int nshot, int nt, float* out, cudaStream_t s);
 void launch_misfit(const float* a, const float* b, long long n, double* partial, int npart, double* out,
                    cudaStream_t s);
-void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp, float* grad, cudaStream_t s);
+void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp, float* grad, const float* vel_chain,
+                        cudaStream_t s);
 void launch_ricker(float f0, float dt, int nt, float* out, cudaStream_t s);
+void launch_prep_dm(const Dims& d, const float* dm, const float* kap, float* dmv, cudaStream_t s);
 void launch_nan_scan(const float* a, long long n, int* err, cudaStream_t s);
 
 // Tile geometry of the 2D steps (kernels.cu).

@@ -30,6 +30,14 @@ __device__ __forceinline__ float leap(float c, float um, float lap, float kap, f
     return num * __frcp_rn(1.0f + eps);
 }
 
+// The same update with an extra source term subtracted before the damping
+// factor (the Born secondary source); src = 0 gives exactly leap().
+__device__ __forceinline__ float leap_src(float c, float um, float lap, float kap, float eps, float src)
+{
+    float num = fmaf(kap, lap, fmaf(eps, um, 2.0f * c - um)) - src;
+    return num * __frcp_rn(1.0f + eps);
+}
+
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ float f4(const float4& v, int i)
@@ -184,6 +192,18 @@ __device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, 
     }
 }
 
+// Born secondary source of four points: dmv .* (u^{n+1} - 2 u^n + u^{n-1}),
+// with dmv = dm v^2 (it enters the update as kap * lap - src).
+__device__ __forceinline__ void born_source(const StepArgs& a, long long so, long long off, float* src)
+{
+    const float4 d = ld4(a.dmv + off);
+    const float4 pa = ld4(a.bs_a + so + off), pb = ld4(a.bs_b + so + off), pc = ld4(a.bs_c + so + off);
+    src[0] = d.x * (pa.x - 2.0f * pb.x + pc.x);
+    src[1] = d.y * (pa.y - 2.0f * pb.y + pc.y);
+    src[2] = d.z * (pa.z - 2.0f * pb.z + pc.z);
+    src[3] = d.w * (pa.w - 2.0f * pb.w + pc.w);
+}
+
 // Writes one thread's four updated points (zeros past Nx) and, in the forward
 // pass, their stored copies; in the adjoint pass adds the imaging term
 // g -= u^k (mu^k - 2 mu^{k+1} + mu^{k+2}) to the loaded accumulator values.
@@ -305,6 +325,8 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
         const long long off = (long long)gz * a.P + gx;
         const int dz = sponge_depth(gz, a.nb, a.nz);
         float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
+        float bsrc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (a.dmv) born_source(a, so, off, bsrc);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int dd = max(sponge_depth(gx + i, a.nb, a.nx), dz);
@@ -312,7 +334,7 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
             const float eps = kap * a.ceps * (float)(dd * dd);
             cen[i] = w[i + 4];
             um[i] = f4(uo[rr], i);
-            out[i] = leap(cen[i], um[i], lap[i], kap, eps);
+            out[i] = leap_src(cen[i], um[i], lap[i], kap, eps, bsrc[i]);
         }
         float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (imaging) {
@@ -920,6 +942,8 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
             const float4 uo = *reinterpret_cast<const float4*>(a.uprev + so + off);
             const int dzy = max(sponge_depth(gz, a.nb, a.nz), sponge_depth(gy, a.nb, a.ny));
             float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
+            float bsrc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (a.dmv) born_source(a, so, off, bsrc);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int dd = max(sponge_depth(gx + i, a.nb, a.nx), dzy);
@@ -927,7 +951,7 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
                 const float eps = kap * a.ceps * (float)(dd * dd);
                 cen[i] = w[i + 4];
                 um[i] = f4(uo, i);
-                out[i] = leap(cen[i], um[i], lap[i], kap, eps);
+                out[i] = leap_src(cen[i], um[i], lap[i], kap, eps, bsrc[i]);
             }
             float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (imaging) {
@@ -1301,7 +1325,18 @@ __global__ void k_collapse_mid(const float* __restrict__ in, long long outer, in
     out[i] = acc;
 }
 
-void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp, float* grad, cudaStream_t s)
+// grad *= -2 / v^3: the gradient with respect to velocity from the one with
+// respect to squared slowness (m = 1/v^2).
+__global__ void k_chain_velocity(const float* __restrict__ vel, long long n, float* __restrict__ grad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = vel[i];
+        grad[i] *= -2.0f / (v * v * v);
+    }
+}
+
+void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp, float* grad, const float* vel_chain,
+                        cudaStream_t s)
 {
     // tmp holds 2 * cell floats: [0, cell) the shot sum, [cell, 2 cell) the x-collapsed sum.
     float* t0 = tmp;
@@ -1319,6 +1354,40 @@ void launch_grad_reduce(const Dims& d, const float* gacc, int nshot, float* tmp,
     } else {
         k_collapse_mid<<<(int)((d.phys + bs - 1) / bs), bs, 0, s>>>(t1, 1, d.Nz, d.nz, d.nb, d.nx, grad);
     }
+    if (vel_chain) {
+        count_launch();
+        k_chain_velocity<<<(int)std::min<long long>((d.phys + bs - 1) / bs, 152 * 8), bs, 0, s>>>(vel_chain, d.phys,
+                                                                                                grad);
+    }
+}
+
+// dmv = Extend(dm) * v^2 on the padded grid (v^2 = kap h^2 / dt^2); pitch columns 0.
+__global__ void k_prep_dm(Dims d, const float* __restrict__ dm, const float* __restrict__ kap, float* __restrict__ dmv)
+{
+    const float s = (d.h / d.dt) * (d.h / d.dt);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.cell; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % d.P);
+        const long long r = i / d.P;
+        const int y = (int)(r % d.Ny);
+        const int z = (int)(r / d.Ny);
+        if (x >= d.Nx) {
+            dmv[i] = 0.0f;
+            continue;
+        }
+        const int jx = min(max(x - d.nb, 0), d.nx - 1);
+        const int jz = min(max(z - d.nb, 0), d.nz - 1);
+        const int jy = d.ndim == 3 ? min(max(y - d.nb, 0), d.ny - 1) : 0;
+        const long long j = ((long long)jz * (d.ndim == 3 ? d.ny : 1) + jy) * d.nx + jx;
+        dmv[i] = dm[j] * kap[i] * s;
+    }
+}
+
+void launch_prep_dm(const Dims& d, const float* dm, const float* kap, float* dmv, cudaStream_t s)
+{
+    long long blocks = (d.cell + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    count_launch();
+    k_prep_dm<<<(int)blocks, 256, 0, s>>>(d, dm, kap, dmv);
 }
 
 __global__ void k_ricker(double f0, double dt, int nt, float* out)

@@ -26,7 +26,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libwave.so")
 
 STORE_CHECKPOINT, STORE_BF16, STORE_FP32 = 0, 1, 2
-OP_FORWARD, OP_ADJOINT, OP_GRADIENT = 0, 1, 2
+OP_FORWARD, OP_ADJOINT, OP_GRADIENT, OP_BORN = 0, 1, 2, 3
+WRT_SLOWNESS2, WRT_VELOCITY = 0, 1
 STATUS = {0: "WAVE_OK", 1: "WAVE_ERR_ARG", 2: "WAVE_ERR_CFL", 3: "WAVE_ERR_GEOMETRY",
           4: "WAVE_ERR_WORKSPACE", 5: "WAVE_ERR_CUDA", 6: "WAVE_ERR_TIMEOUT", 7: "WAVE_ERR_NONFINITE"}
 
@@ -68,8 +69,12 @@ def _lib():
         lib.wave_workspace_size.argtypes = [G, I, I, I, P, I, P, I, I, ctypes.POINTER(ctypes.c_size_t)]
         lib.wave_forward.argtypes = [G, P, I, I, P, P, I, P, P, P, ctypes.c_size_t, P]
         lib.wave_adjoint.argtypes = [G, P, I, I, P, I, P, P, P, P, ctypes.c_size_t, P]
-        lib.wave_gradient.argtypes = [G, P, I, I, P, P, I, P, P, P, P, ctypes.POINTER(ctypes.c_double), I, I, P,
+        lib.wave_gradient.argtypes = [G, P, I, I, P, P, I, P, P, P, P, ctypes.POINTER(ctypes.c_double), I, I, I, P,
                                       ctypes.c_size_t, P]
+        lib.wave_jacobian_adjoint.argtypes = [G, P, I, I, P, P, I, P, P, P, I, I, I, P, ctypes.c_size_t, P]
+        lib.wave_jacobian_adjoint.restype = I
+        lib.wave_born.argtypes = [G, P, I, I, P, P, I, P, P, P, P, ctypes.c_size_t, P]
+        lib.wave_born.restype = I
         lib.wave_ricker.argtypes = [ctypes.c_float, ctypes.c_float, I, P, P]
         lib.wave_checkpoint_schedule.argtypes = [I, I, ctypes.POINTER(ctypes.c_longlong), P, I,
                                                  ctypes.POINTER(ctypes.c_int)]
@@ -242,8 +247,8 @@ def wave_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, rec_xyz, resid: torch.T
 
 def wave_gradient(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, d_obs: torch.Tensor,
                   store: int = STORE_CHECKPOINT, nsnap: int = 64, grad=None, want_dsyn: bool = False,
-                  work: torch.Tensor | None = None, stream=None):
-    """Returns (misfit, dPhi/dm [phys shape], d_syn or None)."""
+                  work: torch.Tensor | None = None, stream=None, wrt: int = WRT_SLOWNESS2):
+    """Returns (misfit, dPhi/dm (or dPhi/dv with wrt=WRT_VELOCITY) [phys shape], d_syn or None)."""
     src = _host_xyz(src_xyz, grid.ndim)
     rec = _host_xyz(rec_xyz, grid.ndim)
     ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
@@ -261,10 +266,53 @@ def wave_gradient(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor,
     phi = ctypes.c_double(0.0)
     g = grid.c()
     st = _lib().wave_gradient(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), po, pg, pds,
-                              ctypes.byref(phi), store, nsnap, work.data_ptr(), work.numel(), _stream(stream))
+                              ctypes.byref(phi), store, nsnap, wrt, work.data_ptr(), work.numel(), _stream(stream))
     if st:
         raise WaveError(st, "wave_gradient")
     return phi.value, grad, dsyn
+
+
+def wave_jacobian_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz,
+                          resid: torch.Tensor, store: int = STORE_CHECKPOINT, nsnap: int = 64,
+                          wrt: int = WRT_SLOWNESS2, grad=None, stream=None) -> torch.Tensor:
+    """J(m)' r summed over shots, on the physical grid (w.r.t. m, or v with wrt=WRT_VELOCITY)."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pw = _dev(wavelet, "wavelet", (ns, grid.nt, nsrc))
+    pr = _dev(resid, "resid", (ns, grid.nt, nrec))
+    if grad is None:
+        grad = torch.empty(grid.phys_shape, dtype=torch.float32, device=vel.device)
+    pg = _dev(grad, "grad", grid.phys_shape)
+    work = _workspace(wave_workspace_size(grid, OP_GRADIENT, src, rec, store, nsnap), vel.device)
+    g = grid.c()
+    st = _lib().wave_jacobian_adjoint(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pr, pg, store,
+                                      nsnap, wrt, work.data_ptr(), work.numel(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_jacobian_adjoint")
+    return grad
+
+
+def wave_born(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, dm: torch.Tensor, data=None,
+              stream=None) -> torch.Tensor:
+    """Born data J(m) dm [nshot][nt][nrec] for a squared-slowness perturbation dm."""
+    src = _host_xyz(src_xyz, grid.ndim)
+    rec = _host_xyz(rec_xyz, grid.ndim)
+    ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
+    pv = _dev(vel, "vel", grid.phys_shape)
+    pw = _dev(wavelet, "wavelet", (ns, grid.nt, nsrc))
+    pdm = _dev(dm, "dm", grid.phys_shape)
+    if data is None:
+        data = torch.empty((ns, grid.nt, nrec), dtype=torch.float32, device=vel.device)
+    pd = _dev(data, "data", (ns, grid.nt, nrec))
+    work = _workspace(wave_workspace_size(grid, OP_BORN, src, rec), vel.device)
+    g = grid.c()
+    st = _lib().wave_born(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pdm, pd, work.data_ptr(),
+                          work.numel(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_born")
+    return data
 
 
 def wave_ricker(f0: float, dt: float, nt: int, device="cuda", out=None, stream=None) -> torch.Tensor:
