@@ -177,6 +177,40 @@ wave_status_t wave_forward_static(const wave_grid_t* grid, const float* vel, int
                                   const float* src_xyz, const float* wavelet, int nrec, const float* rec_xyz,
                                   float* data, void* stream);
 
+/* One problem of an uneven batch: its own 2D grid, model, time axis, one
+ * shot's sources and receivers, observed data, and outputs. */
+typedef struct {
+    wave_grid_t grid;      /* 2D grid of this problem                      */
+    const float* vel;      /* dev [nz][nx] velocity                         */
+    int nsrc;
+    const float* src_xyz;  /* host [nsrc][2]                                */
+    const float* wavelet;  /* dev [nt][nsrc]                                */
+    int nrec;
+    const float* rec_xyz;  /* host [nrec][2]                                */
+    const float* d_obs;    /* dev [nt][nrec]                                */
+    float* grad;           /* dev out [nz][nx] gradient of this problem     */
+    double misfit;         /* out: 1/2 ||F q - d_obs||^2 of this problem    */
+} wave_problem_t;
+
+/* Workspace for wave_gradient_batch (store: WAVE_STORE_BF16 or _FP32). */
+wave_status_t wave_workspace_size_batch(const wave_problem_t* probs, int nprob, int store, size_t* bytes);
+
+/* FWI gradients of nprob independent 2D problems of different sizes, time
+ * axes and models (each problem is the gradient of wave_gradient for its own
+ * single shot), computed together: one persistent forward sweep that stores
+ * every level (store = WAVE_STORE_BF16 or WAVE_STORE_FP32) and one persistent
+ * adjoint sweep, in which each 128 x 32 tile advances as soon as its
+ * neighbours have finished the previous step (bounded waits; a wait that
+ * runs out returns WAVE_ERR_TIMEOUT).  The time loop has no per-step launch
+ * and no global barrier, so short problems leave the sweep early.  With
+ * use_graph != 0 the device work after the set-up is captured once into a
+ * CUDA graph and replayed by later calls with the same problems and buffers.
+ * Each problem's misfit field is written on return.  The batch is the
+ * paper's per-shot parallelism of the gradient (section "Putting it all
+ * together": gradients of randomly drawn shots per iteration). */
+wave_status_t wave_gradient_batch(wave_problem_t* probs, int nprob, int store, int wrt, int use_graph, void* work,
+                                  size_t work_bytes, void* stream);
+
 /* Ricker wavelet q(t_n) = (1 - 2 a) exp(-a), a = (pi f0 (n dt - 1/f0))^2,
  * n = 0..nt-1 (the wavelet of the paper's FWI example, peak delayed by 1/f0).
  *   out dev out [nt] */
@@ -230,6 +264,10 @@ int wave_variant_count(int which);
 wave_status_t wave_autotune(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
                             const float* wavelet, int nrec, const float* rec_xyz, int steps, void* work,
                             size_t work_bytes, void* stream, int* best_fwd, int* best_adj);
+
+/* Name of the last failing CUDA runtime call in this thread (for
+ * WAVE_ERR_CUDA diagnostics; "cudaSuccess" if none). */
+const char* wave_cuda_error_name(void);
 
 /* Largest stable dt * vmax / h for ndim = 2 or 3 (0 for other ndim). */
 double wave_courant_limit(int ndim);

@@ -41,3 +41,24 @@ class ForwardModel(torch.autograd.Function):
 def forward_model(vel, wavelet, grid, src_xyz, rec_xyz, store=wave.STORE_CHECKPOINT, nsnap=64):
     """Shot records with autograd support for vel and wavelet."""
     return ForwardModel.apply(vel, wavelet, grid, src_xyz, rec_xyz, store, nsnap)
+
+
+class BatchMisfit(torch.autograd.Function):
+    """Misfits of an uneven batch of problems as a differentiable function of
+    their velocity models: forward runs wave_gradient_batch once (both sweeps)
+    and keeps the velocity gradients for the backward pass."""
+
+    @staticmethod
+    def forward(ctx, problems, store, use_graph, *vels):
+        misfits, grads = wave.wave_gradient_batch(problems, store=store, wrt=wave.WRT_VELOCITY, use_graph=use_graph)
+        ctx.grads = grads
+        return torch.tensor(misfits, dtype=torch.float64, device=vels[0].device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        return (None, None, None) + tuple(g * gout[i].to(g.dtype) for i, g in enumerate(ctx.grads))
+
+
+def batch_misfit(problems, store=wave.STORE_BF16, use_graph=True):
+    """Per-problem misfits [nprob] with gradients flowing to each problem's vel."""
+    return BatchMisfit.apply(problems, store, use_graph, *[p.vel for p in problems])

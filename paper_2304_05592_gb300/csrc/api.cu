@@ -192,7 +192,9 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
 
 #define CK(x)                         \
     do {                              \
-        if ((x) != cudaSuccess) {     \
+        cudaError_t e_ = (x);         \
+        if (e_ != cudaSuccess) {      \
+            note_cuda_error(e_);      \
             (void)cudaGetLastError(); \
             return WAVE_ERR_CUDA;     \
         }                             \

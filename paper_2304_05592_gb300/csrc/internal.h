@@ -157,6 +157,9 @@ int current_variant(int which);           // the selected or default variant
 int select_variant(int which, int v);     // v = -1 restores the default; 0 on success
 bool variant_forced(int which);           // true after wave_set_variant(which, v >= 0)
 
+// Remembers the last failing CUDA call of this thread (profile.cu).
+void note_cuda_error(cudaError_t e);
+
 // Launch accounting and sampled per-launch timing of the stencil kernels
 // (profile.cu).  Every launcher above calls count_launch(); launch_step wraps
 // sampled launches in a pair of CUDA events on the launching stream.

@@ -34,7 +34,14 @@ cudaEvent_t take_event()
     return g_pool[g_pool_next++];
 }
 
+thread_local cudaError_t t_last_error = cudaSuccess;
+
 }  // namespace
+
+void note_cuda_error(cudaError_t e)
+{
+    if (e != cudaSuccess) t_last_error = e;
+}
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -64,6 +71,8 @@ using namespace wave;
 extern "C" {
 
 long long wave_launch_count(void) { return g_launches.load(); }
+
+const char* wave_cuda_error_name(void) { return cudaGetErrorName(t_last_error); }
 
 wave_status_t wave_profile_start(int every)
 {

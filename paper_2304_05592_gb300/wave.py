@@ -36,6 +36,8 @@ class WaveError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         msg = _lib().wave_status_str(status).decode() if _LIB is not None else ""
+        if status == 5 and _LIB is not None:
+            msg += ", " + _lib().wave_cuda_error_name().decode()
         super().__init__(f"{what}: {STATUS.get(status, status)} ({msg})")
 
 
@@ -43,6 +45,13 @@ class wave_grid_t(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("nb", ctypes.c_int), ("nt", ctypes.c_int), ("h", ctypes.c_float), ("dt", ctypes.c_float),
                 ("vref", ctypes.c_float)]
+
+
+class wave_problem_t(ctypes.Structure):
+    _fields_ = [("grid", wave_grid_t), ("vel", ctypes.c_void_p), ("nsrc", ctypes.c_int),
+                ("src_xyz", ctypes.c_void_p), ("wavelet", ctypes.c_void_p), ("nrec", ctypes.c_int),
+                ("rec_xyz", ctypes.c_void_p), ("d_obs", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+                ("misfit", ctypes.c_double)]
 
 
 _LIB = None
@@ -80,6 +89,8 @@ def _lib():
                                                  ctypes.POINTER(ctypes.c_int)]
         lib.wave_courant_limit.argtypes = [I]
         lib.wave_courant_limit.restype = ctypes.c_double
+        lib.wave_cuda_error_name.argtypes = []
+        lib.wave_cuda_error_name.restype = ctypes.c_char_p
         lib.wave_status_str.argtypes = [I]
         lib.wave_status_str.restype = ctypes.c_char_p
         lib.wave_forward_static.argtypes = [G, P, I, I, P, P, I, P, P, P]
@@ -87,6 +98,11 @@ def _lib():
         lib.wave_autotune.argtypes = [G, P, I, I, P, P, I, P, I, P, ctypes.c_size_t, P,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         lib.wave_autotune.restype = I
+        lib.wave_workspace_size_batch.argtypes = [ctypes.POINTER(wave_problem_t), I, I,
+                                                  ctypes.POINTER(ctypes.c_size_t)]
+        lib.wave_workspace_size_batch.restype = I
+        lib.wave_gradient_batch.argtypes = [ctypes.POINTER(wave_problem_t), I, I, I, I, P, ctypes.c_size_t, P]
+        lib.wave_gradient_batch.restype = I
         lib.wave_set_variant.argtypes = [I, I]
         lib.wave_set_variant.restype = I
         lib.wave_variant_count.argtypes = [I]
@@ -395,3 +411,61 @@ def wave_autotune(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor,
     if st:
         raise WaveError(st, "wave_autotune")
     return bf.value, ba.value
+
+
+class BatchProblem:
+    """One problem of an uneven batch: Grid, velocity (CUDA), source and
+    receiver coordinates (host, [n][2]), wavelet [nt][nsrc] and observed data
+    [nt][nrec] (CUDA)."""
+
+    def __init__(self, grid: Grid, vel, src_xyz, wavelet, rec_xyz, d_obs):
+        self.grid, self.vel, self.wavelet, self.d_obs = grid, vel, wavelet, d_obs
+        self.src = np.ascontiguousarray(np.asarray(src_xyz, np.float32).reshape(-1, 2))
+        self.rec = np.ascontiguousarray(np.asarray(rec_xyz, np.float32).reshape(-1, 2))
+
+
+def _problem_array(problems, grads):
+    arr = (wave_problem_t * max(len(problems), 1))()
+    for i, (p, gr) in enumerate(zip(problems, grads)):
+        _dev(p.vel, "vel", p.grid.phys_shape)
+        _dev(p.wavelet, "wavelet", (p.grid.nt, p.src.shape[0]))
+        _dev(p.d_obs, "d_obs", (p.grid.nt, p.rec.shape[0]))
+        arr[i].grid = p.grid.c()
+        arr[i].vel = p.vel.data_ptr()
+        arr[i].nsrc = p.src.shape[0]
+        arr[i].src_xyz = p.src.ctypes.data if p.src.size else None
+        arr[i].wavelet = p.wavelet.data_ptr()
+        arr[i].nrec = p.rec.shape[0]
+        arr[i].rec_xyz = p.rec.ctypes.data if p.rec.size else None
+        arr[i].d_obs = p.d_obs.data_ptr()
+        arr[i].grad = gr.data_ptr() if gr is not None else None
+    return arr
+
+
+def wave_gradient_batch(problems, store: int = STORE_BF16, wrt: int = WRT_SLOWNESS2, use_graph: bool = True,
+                        grads=None, work: torch.Tensor | None = None, stream=None):
+    """Gradients and misfits of an uneven batch of 2D problems (one persistent
+    forward sweep, one persistent adjoint sweep).  Returns (misfits, grads)."""
+    if grads is None:
+        grads = [torch.empty(p.grid.phys_shape, dtype=torch.float32, device=p.vel.device) for p in problems]
+    arr = _problem_array(problems, grads)
+    nbytes = ctypes.c_size_t(0)
+    st = _lib().wave_workspace_size_batch(arr, len(problems), store, ctypes.byref(nbytes))
+    if st:
+        raise WaveError(st, "wave_workspace_size_batch")
+    if work is None or work.numel() < nbytes.value:
+        work = _workspace(nbytes.value, problems[0].vel.device if problems else "cuda")
+    st = _lib().wave_gradient_batch(arr, len(problems), store, wrt, int(use_graph), work.data_ptr(), work.numel(),
+                                    _stream(stream))
+    if st:
+        raise WaveError(st, "wave_gradient_batch")
+    return [arr[i].misfit for i in range(len(problems))], grads
+
+
+def wave_workspace_size_batch(problems, store: int = STORE_BF16) -> int:
+    arr = _problem_array(problems, [None] * len(problems))
+    nbytes = ctypes.c_size_t(0)
+    st = _lib().wave_workspace_size_batch(arr, len(problems), store, ctypes.byref(nbytes))
+    if st:
+        raise WaveError(st, "wave_workspace_size_batch")
+    return int(nbytes.value)
