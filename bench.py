@@ -179,6 +179,74 @@ def cpu_baseline(nt: int):
             "sample": f"1 shot of the 32 (full grid, nt={nt}), one gradient, FP64, {el:.1f} s"}
 
 
+def config3_forward(dev, peak):
+    """3D config-3 forward (400 x 400 x 300 at 10 m, 160 000 receivers), 200 steps."""
+    import torch
+
+    from paper_2304_05592_gb300 import synth, wave
+    from paper_2304_05592_gb300.wave import Grid
+
+    p = synth.config3(nt=200)
+    g = Grid.of(p)
+    v = torch.from_numpy(p.vel).to(dev)
+    q = wave.wave_ricker(p.f0, p.dt, p.nt, device=dev)[None, :, None].contiguous()
+    wave.wave_forward(g, v, p.src, q, p.rec)
+    torch.cuda.synchronize()
+    wave.wave_profile_start(1)
+    t = time.perf_counter()
+    wave.wave_forward(g, v, p.src, q, p.rec)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    fms, fn, _, _ = wave.wave_profile_stop()
+    avg = fms / max(fn, 1) / 1e3
+    N = p.padded_points
+    ach = 16 * N / avg / 1e9
+    return {"workload": "3D forward 400x400x300 at 10 m + 40-cell sponge (480x480x380 padded), 160000 receivers, "
+                        "200 of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
+            "kernel": "k_step3d<8,32,fwd>", "avg_launch_us": avg * 1e6, "achieved_gbs": ach, "frac": ach / peak,
+            "bound": "hbm", "bytes_per_point": 16}
+
+
+def uneven_batch(dev):
+    """Config 4: 64 shots of different grids, models and nt; one batched call
+    (persistent sweeps, CUDA graph, BF16 store) against one call per shot."""
+    import torch
+
+    from paper_2304_05592_gb300 import synth, wave
+    from paper_2304_05592_gb300.wave import BatchProblem, Grid
+
+    probs = synth.uneven_batch(seed=4, nshot=64)
+    bps = []
+    pts = 0
+    for pb in probs:
+        g = Grid.of(pb)
+        q = wave.wave_ricker(pb.f0, pb.dt, pb.nt, device=dev)[:, None].contiguous()
+        v = torch.from_numpy(pb.vel).to(dev)
+        dob = wave.wave_forward(g, v, pb.src, q[None].contiguous(), pb.rec)[0].contiguous()
+        bps.append(BatchProblem(g, (v * 1.02).contiguous(), pb.src[0], q, pb.rec[0], dob))
+        pts += 2 * (pb.nt - 1) * pb.padded_points
+    ws = wave.wave_workspace_size_batch(bps)
+    work = torch.empty(ws, dtype=torch.uint8, device=dev)
+    wave.wave_gradient_batch(bps, work=work)  # captures the graph
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    wave.wave_gradient_batch(bps, work=work)
+    torch.cuda.synchronize()
+    el_b = time.perf_counter() - t
+    del work
+    torch.cuda.empty_cache()
+    t = time.perf_counter()
+    for bp in bps:
+        wave.wave_gradient(bp.grid, bp.vel, bp.src[None], bp.wavelet[None].contiguous(), bp.rec[None],
+                           bp.d_obs[None].contiguous(), store=wave.STORE_BF16)
+    torch.cuda.synchronize()
+    el_p = time.perf_counter() - t
+    return {"workload": "64 2D shots, nx 256-768, nz 128-384, h 6.25-12.5 m, nt 1500-4000, layered models, "
+                        "BF16 store", "shot_gradients_per_s_batched": len(bps) / el_b,
+            "shot_gradients_per_s_one_call_per_shot": len(bps) / el_p, "pt_updates_per_s_batched": pts / el_b,
+            "workspace_gb": ws / 1e9, "batched": "2 persistent sweeps in a CUDA graph"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -354,6 +422,12 @@ def main():
         el = time.perf_counter() - t0
         line["e2e"] = {"value": ne * p.nshot / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h}
+        del work
+        torch.cuda.empty_cache()
+        line["config3_forward"] = config3_forward(dev, peak)
+        torch.cuda.empty_cache()
+        line["uneven_batch"] = uneven_batch(dev)
+        torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p.nt)
     if rank == 0:

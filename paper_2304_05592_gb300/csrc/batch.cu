@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "stencil.cuh"
 
 namespace wave {
 
@@ -75,8 +76,6 @@ __global__ void __launch_bounds__(32 * kBBZ, 2)
     __shared__ __align__(16) float s[kBTZ + 8][SW];
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int lx = 4 * threadIdx.x;
-    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
-
     for (int step = 0; step < nsteps; ++step) {
         for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
             const BProb& p = probs[tile_prob[t]];
@@ -134,32 +133,28 @@ __global__ void __launch_bounds__(32 * kBBZ, 2)
                 const float4 C = *reinterpret_cast<const float4*>(row + 8);
                 const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
                 float lap[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
-                             kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
-#pragma unroll
-                for (int k = 1; k <= 4; ++k) {
-                    const float4 U = *reinterpret_cast<const float4*>(&s[r + 4 - k][lx + 4]);
-                    const float4 D = *reinterpret_cast<const float4*>(&s[r + 4 + k][lx + 4]);
-                    lap[0] += ck[k] * (U.x + D.x);
-                    lap[1] += ck[k] * (U.y + D.y);
-                    lap[2] += ck[k] * (U.z + D.z);
-                    lap[3] += ck[k] * (U.w + D.w);
-                }
+                lap4(w, [&](int k, float4& U, float4& D) {
+                    U = *reinterpret_cast<const float4*>(&s[r + 4 - k][lx + 4]);
+                    D = *reinterpret_cast<const float4*>(&s[r + 4 + k][lx + 4]);
+                }, lap);
                 const float4 kp = __ldg(reinterpret_cast<const float4*>(p.kap + off));
                 const float4 uo = ldcg4(un + off);
                 const float kv[4] = {kp.x, kp.y, kp.z, kp.w};
                 const float ov[4] = {uo.x, uo.y, uo.z, uo.w};
+                const float cv[4] = {w[4], w[5], w[6], w[7]};
+                const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
                 const int dz = bdepth(gz, p.nb, p.nz);
-                float out[4];
+                float out[4], ev[4], iv[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(bdepth(gx + e, p.nb, p.nx), dz);
-                    const float eps = kv[e] * p.ceps * (float)(dd * dd);
-                    const float num = fmaf(kv[e], lap[e], fmaf(eps, ov[e], 2.0f * w[e + 4] - ov[e]));
-                    out[e] = e < nvalid ? num * __frcp_rn(1.0f + eps) : 0.0f;
+                    ev[e] = kv[e] * p.ceps * (float)(dd * dd);
+                    iv[e] = __frcp_rn(1.0f + ev[e]);
                 }
+                update4(cv, ov, lap, kv, ev, iv, zero4, out);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e >= nvalid) out[e] = 0.0f;
                 *reinterpret_cast<float4*>(un + off) = make_float4(out[0], out[1], out[2], out[3]);
                 if (!ADJ) {
                     const long long so = (long long)(n + 1) * p.cell + off;

@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "stencil.cuh"
 
 namespace wave {
 
@@ -260,7 +261,7 @@ __device__ __forceinline__ void zero_padding(const StepArgs& a, long long so, lo
 // values outside the padded grid read as zero.  The pointwise inputs of the
 // thread's rows are loaded before the halo tile so that their latency overlaps.
 template <int TZ, int BZ, bool ADJ>
-__global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
+__global__ void __launch_bounds__(32 * BZ, 1024 / (32 * BZ)) k_step2d(const StepArgs a)
 {
     constexpr int SW = kTX + 8;
     constexpr int RB = TZ / BZ;
@@ -295,7 +296,6 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
     }
     __syncthreads();
 
-    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
         const int r = threadIdx.y + rr * BZ;
@@ -309,19 +309,10 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
         const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
         const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
         float lap[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            lap[i] = 2.0f * kC0 * w[i + 4] + kC1 * (w[i + 3] + w[i + 5]) + kC2 * (w[i + 2] + w[i + 6]) +
-                     kC3 * (w[i + 1] + w[i + 7]) + kC4 * (w[i] + w[i + 8]);
-#pragma unroll
-        for (int k = 1; k <= 4; ++k) {
-            const float4 U = lds4(&s[r + 4 - k][lx + 4]);
-            const float4 D = lds4(&s[r + 4 + k][lx + 4]);
-            lap[0] += ck[k] * (U.x + D.x);
-            lap[1] += ck[k] * (U.y + D.y);
-            lap[2] += ck[k] * (U.z + D.z);
-            lap[3] += ck[k] * (U.w + D.w);
-        }
+        lap4(w, [&](int k, float4& U, float4& D) {
+            U = lds4(&s[r + 4 - k][lx + 4]);
+            D = lds4(&s[r + 4 + k][lx + 4]);
+        }, lap);
         const long long off = (long long)gz * a.P + gx;
         const int dz = sponge_depth(gz, a.nb, a.nz);
         float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
@@ -334,7 +325,7 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d(const StepArgs a)
             const float eps = kap * a.ceps * (float)(dd * dd);
             cen[i] = w[i + 4];
             um[i] = f4(uo[rr], i);
-            out[i] = leap_src(cen[i], um[i], lap[i], kap, eps, bsrc[i]);
+            out[i] = leap1(cen[i], um[i], lap[i], kap, eps, __frcp_rn(1.0f + eps), bsrc[i]);
         }
         float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (imaging) {
@@ -433,7 +424,6 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
         cp_async_commit();
     };
 
-    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
     load_tile(0, s0);
     for (int shot = s0; shot < s1; ++shot) {
         const int cur = (shot - s0) & 1;
@@ -479,26 +469,19 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
             const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
             const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
-                         kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
-#pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                const float4 U = lds4(&s[cur][r + 4 - k][lx + 4]);
-                const float4 D = lds4(&s[cur][r + 4 + k][lx + 4]);
-                lap[0] += ck[k] * (U.x + D.x);
-                lap[1] += ck[k] * (U.y + D.y);
-                lap[2] += ck[k] * (U.z + D.z);
-                lap[3] += ck[k] * (U.w + D.w);
-            }
-            float out[4], cen[4], um[4];
+            lap4(w, [&](int k, float4& U, float4& D) {
+                U = lds4(&s[cur][r + 4 - k][lx + 4]);
+                D = lds4(&s[cur][r + 4 + k][lx + 4]);
+            }, lap);
+            float out[4], cen[4], um[4], kv[4];
+            const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 cen[e] = w[e + 4];
                 um[e] = f4(uo[rr], e);
-                out[e] = fmaf(f4(kp[rr], e), lap[e], fmaf(eps[rr][e], um[e], 2.0f * cen[e] - um[e])) * inv[rr][e];
+                kv[e] = f4(kp[rr], e);
             }
+            update4(cen, um, lap, kv, eps[rr], inv[rr], zero4, out);
             write4<ADJ>(a, so, (long long)gz * a.P + gx, nvalid, out, cen, um, false, nullptr,
                         make_float4(0.f, 0.f, 0.f, 0.f));
             if (imaging) {
@@ -600,7 +583,6 @@ __global__ void __launch_bounds__(32 * NW) k_step2d_zm(const StepArgs a)
         fq[d] = ldf(zs + d);
         gq[d] = ldg(zs + d);
     }
-    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
     for (int z = zs; z < ze; ++z) {
         q[8] = ldu(z + 4);
         const float4 hc = hq[0], pc = pq[0], kc = kq[0], fc = fq[0], gc = gq[0];
@@ -634,37 +616,27 @@ __global__ void __launch_bounds__(32 * NW) k_step2d_zm(const StepArgs a)
         if (nvalid > 0) {
             const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
+            lap4(w, [&](int k, float4& U, float4& D) {
+                U = q[4 - k];
+                D = q[4 + k];
+            }, lap);
+            float out[4], kv[4];
+            const float cen[4] = {B.x, B.y, B.z, B.w}, um[4] = {pc.x, pc.y, pc.z, pc.w};
+            const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
-                         kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
-#pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                lap[0] += ck[k] * (q[4 - k].x + q[4 + k].x);
-                lap[1] += ck[k] * (q[4 - k].y + q[4 + k].y);
-                lap[2] += ck[k] * (q[4 - k].z + q[4 + k].z);
-                lap[3] += ck[k] * (q[4 - k].w + q[4 + k].w);
-            }
-            float out[4], cen[4], um[4];
-            const bool interior = xin && z >= a.nb && z <= a.nb + a.nz - 1;
-            if (interior) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    cen[e] = w[e + 4];
-                    um[e] = f4(pc, e);
-                    out[e] = fmaf(f4(kc, e), lap[e], 2.0f * cen[e] - um[e]);
-                }
+            for (int e = 0; e < 4; ++e) kv[e] = f4(kc, e);
+            if (xin && z >= a.nb && z <= a.nb + a.nz - 1) {
+                update4_interior(cen, um, lap, kv, out);
             } else {
+                float ev[4], iv[4];
                 const int dz = sponge_depth(z, a.nb, a.nz);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
-                    const float kap = f4(kc, e);
-                    const float eps = kap * a.ceps * (float)(dd * dd);
-                    cen[e] = w[e + 4];
-                    um[e] = f4(pc, e);
-                    out[e] = leap(cen[e], um[e], lap[e], kap, eps);
+                    ev[e] = kv[e] * a.ceps * (float)(dd * dd);
+                    iv[e] = __frcp_rn(1.0f + ev[e]);
                 }
+                update4(cen, um, lap, kv, ev, iv, zero4, out);
             }
             const float uf[4] = {fc.x, fc.y, fc.z, fc.w};
             write4<ADJ>(a, so, off, nvalid, out, cen, um, imaging, uf, gc);
@@ -758,7 +730,6 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) k_step2d_tma(const __grid_co
         }
     }
 
-    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
     const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
     for (int i = 0;; ++i) {
         const int t = blockIdx.x + i * gridDim.x;
@@ -803,31 +774,26 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) k_step2d_tma(const __grid_co
                 const float4 B = q[4];
                 const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
                 float lap[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    lap[e] = 2.0f * kC0 * w[e + 4] + kC1 * (w[e + 3] + w[e + 5]) + kC2 * (w[e + 2] + w[e + 6]) +
-                             kC3 * (w[e + 1] + w[e + 7]) + kC4 * (w[e] + w[e + 8]);
-#pragma unroll
-                for (int k = 1; k <= 4; ++k) {
-                    lap[0] += ck[k] * (q[4 - k].x + q[4 + k].x);
-                    lap[1] += ck[k] * (q[4 - k].y + q[4 + k].y);
-                    lap[2] += ck[k] * (q[4 - k].z + q[4 + k].z);
-                    lap[3] += ck[k] * (q[4 - k].w + q[4 + k].w);
-                }
+                lap4(w, [&](int k, float4& U, float4& D) {
+                    U = q[4 - k];
+                    D = q[4 + k];
+                }, lap);
                 const float4 kp = lds4(sk + r * kTX + 4 * lane);
                 const float4 uo = lds4(sp + r * kTX + 4 * lane);
                 const int dz = sponge_depth(gz, a.nb, a.nz);
-                float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f};
+                float out[4], cen[4], um[4], uf[4] = {0.f, 0.f, 0.f, 0.f}, kv[4], ev[4], iv[4];
+                const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
                 float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
-                    const float kap = f4(kp, e);
-                    const float eps = kap * a.ceps * (float)(dd * dd);
+                    kv[e] = f4(kp, e);
+                    ev[e] = kv[e] * a.ceps * (float)(dd * dd);
+                    iv[e] = __frcp_rn(1.0f + ev[e]);
                     cen[e] = w[e + 4];
                     um[e] = f4(uo, e);
-                    out[e] = leap(cen[e], um[e], lap[e], kap, eps);
                 }
+                update4(cen, um, lap, kv, ev, iv, zero4, out);
                 if (imaging) {
                     if (uf_bf16) {
                         unpack_bf16x4(*reinterpret_cast<const uint2*>(

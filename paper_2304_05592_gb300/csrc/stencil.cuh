@@ -1,0 +1,63 @@
+// stencil.cuh -- the per-point arithmetic of the 2D step, shared by every 2D
+// kernel so that all of them produce the same bits.  The evaluation order is
+// fixed by explicit fmaf calls rather than left to contraction.
+#pragma once
+
+#include "internal.h"
+
+namespace wave {
+
+// 8th-order Laplacian (unit spacing) of 4 consecutive x points.  w[0..11] are
+// the row values x-4 .. x+7 (the points are w[4..7]); zn(k) returns the pair
+// (values k rows above, values k rows below) of the 4 points, k = 1..4, and is
+// called in the loop so that the loads interleave with the arithmetic.
+// Evaluation order: 2 c0 w, then + c_k (w_{-k} + w_{+k}) for k = 1..4 along x,
+// then along z.
+template <class ZN>
+__device__ __forceinline__ void lap4(const float* w, ZN zn, float* lap)
+{
+    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float acc = (2.0f * kC0) * w[e + 4];
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) acc = fmaf(ck[k], w[e + 4 - k] + w[e + 4 + k], acc);
+        lap[e] = acc;
+    }
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        float4 U, D;
+        zn(k, U, D);
+        lap[0] = fmaf(ck[k], U.x + D.x, lap[0]);
+        lap[1] = fmaf(ck[k], U.y + D.y, lap[1]);
+        lap[2] = fmaf(ck[k], U.z + D.z, lap[2]);
+        lap[3] = fmaf(ck[k], U.w + D.w, lap[3]);
+    }
+}
+
+// Leapfrog update of one point: (kap lap + eps um + 2 c - um - src) * inv,
+// inv = 1 / (1 + eps); src is the Born secondary source (zero elsewhere).
+__device__ __forceinline__ float leap1(float c, float um, float lap, float kap, float eps, float inv, float src)
+{
+    const float t = fmaf(kap, lap, fmaf(eps, um, fmaf(2.0f, c, -um)));
+    return (t - src) * inv;
+}
+
+// The same for 4 points.
+__device__ __forceinline__ void update4(const float* c, const float* um, const float* lap, const float* kap,
+                                        const float* eps, const float* inv, const float* src, float* out)
+{
+#pragma unroll
+    for (int e = 0; e < 4; ++e) out[e] = leap1(c[e], um[e], lap[e], kap[e], eps[e], inv[e], src[e]);
+}
+
+// The same update where the sponge is absent (eps = 0, inv = 1) and there is no
+// secondary source: equal to update4 up to the sign of zero results.
+__device__ __forceinline__ void update4_interior(const float* c, const float* um, const float* lap, const float* kap,
+                                                 float* out)
+{
+#pragma unroll
+    for (int e = 0; e < 4; ++e) out[e] = fmaf(kap[e], lap[e], fmaf(2.0f, c[e], -um[e]));
+}
+
+}  // namespace wave
