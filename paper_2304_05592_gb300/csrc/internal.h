@@ -142,10 +142,11 @@ constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile h
 
 // 2D kernel variants: direct loads (kind 0), the persistent TMA pipeline
 // (kind 1) with tile height TZ, R rows per warp and NST stages, shot groups
-// (kind 2): one CTA runs its tile for G shots (R = thread rows), or the
+// (kind 2): one CTA runs its tile for G shots (R = thread rows), the
 // z-march (kind 3): one warp per TZ-row strip, R warps per CTA, prefetch
-// distance NST rows.  With kind 2
-// in the adjoint, the gradient buffer holds one accumulator per shot group.
+// distance NST rows, or shot groups fed by TMA (kind 4, fields as kind 2).
+// With kinds 2 and 4 in the adjoint, the gradient buffer holds one
+// accumulator per shot group.
 struct Variant2D {
     int kind, TZ, R, NST, G;
 };

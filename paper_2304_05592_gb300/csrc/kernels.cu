@@ -520,6 +520,187 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// 2D step, shot groups fed by TMA.  As the shot-group kernel, but each shot's
+// (TZ+8) x 136 halo tile of u arrives by one TMA load (zero fill outside the
+// padded grid) into a two-stage ring: the load of shot i+1 is issued by one
+// thread while shot i is computed.  Row offsets, the model and the sponge
+// factors are set up once per CTA in 32-bit form, so the per-shot work is the
+// stencil arithmetic, one load of the previous level and one store per 4
+// points.  Waits on the ring are bounded; on a timeout the CTA records
+// kErrTimeout, lets its issued copies land and returns.
+template <int TZ, int BZ, int G, bool ADJ>
+__global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ))
+    k_step2d_sgt(const __grid_constant__ StepMaps mp, const StepArgs a)
+{
+    constexpr int SW = kTX + 8;
+    constexpr int RB = TZ / BZ;
+    constexpr int SU = (TZ + 8) * SW;  // floats in one stage
+    static_assert(SU % 32 == 0, "stages must stay 128-byte aligned");
+    extern __shared__ unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar[2];
+    float* st = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
+    float* sg = st + 2 * SU;  // [TZ][kTX] gradient tile (adjoint with imaging)
+    const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * kTX, z0 = blockIdx.y * TZ;
+    const int grp = blockIdx.z, s0 = grp * G, ns = min(G, a.nshot - s0);
+    const int lx = 4 * tx, gx = x0 + lx;
+    const int nvalid = min(4, a.Nx - gx);
+    const bool imaging = ADJ && a.gacc != nullptr;
+    const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
+    constexpr uint32_t kBytes = SU * 4u;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], kBytes);
+        tma_load_4d(st, mh, &bar[0], x0 - 4, z0 - 4, s0, a.u_buf);
+    }
+
+    int off[RB];
+    bool live[RB], pad[RB];
+    float4 kp[RB];
+    float eps[RB][4], inv[RB][4];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+        const int gz = z0 + ty + rr * BZ;
+        off[rr] = gz * a.P + gx;
+        live[rr] = gz < a.Nz && nvalid > 0;
+        pad[rr] = gz < a.Nz && nvalid <= 0 && gx < a.P;
+        kp[rr] = live[rr] ? ld4(a.kap + off[rr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int dz = sponge_depth(gz, a.nb, a.nz);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
+            eps[rr][e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
+            inv[rr][e] = __frcp_rn(1.0f + eps[rr][e]);
+        }
+    }
+    float* gq = imaging ? a.gacc + (size_t)grp * a.cell : nullptr;
+    if (imaging) {
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (live[rr]) v = *reinterpret_cast<const float4*>(gq + off[rr]);
+            *reinterpret_cast<float4*>(sg + r * kTX + lx) = v;
+        }
+    }
+
+    for (int i = 0; i < ns; ++i) {
+        const int shot = s0 + i, stage = i & 1;
+        if (tid == 0 && i + 1 < ns) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[stage ^ 1], kBytes);
+            tma_load_4d(st + (stage ^ 1) * SU, mh, &bar[stage ^ 1], x0 - 4, z0 - 4, shot + 1, a.u_buf);
+        }
+        const size_t so = (size_t)shot * a.cell;
+        float4 uo[RB];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+            uo[rr] = live[rr] ? *reinterpret_cast<const float4*>(a.uprev + so + off[rr])
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(a.err, kErrTimeout);
+                // copies issued by this CTA may still land in its shared memory
+                mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
+                if (i + 1 < ns) mbar_wait(&bar[stage ^ 1], (uint32_t)((i + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        const float* sb = st + stage * SU;
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ;
+            float* un = a.unew + so + off[rr];
+            if (!live[rr]) {
+                if (pad[rr]) *reinterpret_cast<float4*>(un) = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            const float* row = sb + (r + 4) * SW + lx;
+            const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+            float lap[4];
+            lap4(w, [&](int k, float4& U, float4& D) {
+                U = lds4(row + 4 - k * SW);
+                D = lds4(row + 4 + k * SW);
+            }, lap);
+            const float cen[4] = {B.x, B.y, B.z, B.w};
+            const float um[4] = {uo[rr].x, uo[rr].y, uo[rr].z, uo[rr].w};
+            const float kv[4] = {kp[rr].x, kp[rr].y, kp[rr].z, kp[rr].w};
+            const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+            float out[4];
+            update4(cen, um, lap, kv, eps[rr], inv[rr], zero4, out);
+            // a full float4: points past Nx stay the zero exterior
+            *reinterpret_cast<float4*>(un) = make_float4(out[0], nvalid > 1 ? out[1] : 0.0f,
+                                                         nvalid > 2 ? out[2] : 0.0f, nvalid > 3 ? out[3] : 0.0f);
+            if (!ADJ) {
+                if (a.st16) {
+                    if (nvalid == 4) {
+                        store_bf16x4(a.st16 + so + off[rr], out);
+                    } else {
+                        for (int e = 0; e < nvalid; ++e) a.st16[so + off[rr] + e] = __float2bfloat16_rn(out[e]);
+                    }
+                }
+                if (a.st32) {
+                    if (nvalid == 4) {
+                        *reinterpret_cast<float4*>(a.st32 + so + off[rr]) = make_float4(out[0], out[1], out[2], out[3]);
+                    } else {
+                        for (int e = 0; e < nvalid; ++e) a.st32[so + off[rr] + e] = out[e];
+                    }
+                }
+            } else if (imaging) {
+                float uf[4];
+                if (a.uf16) {
+                    unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off[rr]), uf);
+                } else {
+                    const float4 v = ld4(a.uf32 + so + off[rr]);
+                    uf[0] = v.x;
+                    uf[1] = v.y;
+                    uf[2] = v.z;
+                    uf[3] = v.w;
+                }
+                float* g = sg + r * kTX + lx;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) g[e] -= uf[e] * (out[e] - 2.0f * cen[e] + um[e]);
+            }
+        }
+        __syncthreads();  // the stage has been read and this shot's points are written
+        if (sparse) {
+            const int kcell = TZ / a.TZc;
+            const int cbase = (shot * a.ncx + (int)blockIdx.x) * a.ncz;
+            const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
+            int ib = 0, ie = 0, gb = 0, ge = 0;
+            if (a.inj.cell_start) {
+                ib = a.inj.cell_start[cbase + c0];
+                ie = a.inj.cell_start[cbase + c1];
+            }
+            if (a.gat.cell_start) {
+                gb = a.gat.cell_start[cbase + c0];
+                ge = a.gat.cell_start[cbase + c1];
+            }
+            sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * BZ, imaging ? sg : nullptr, z0, x0);
+            if (imaging) __syncthreads();  // injection terms land in the gradient tile before the next shot
+        }
+    }
+    if (imaging) {
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ;
+            if (live[rr])
+                *reinterpret_cast<float4*>(gq + off[rr]) = *reinterpret_cast<const float4*>(sg + r * kTX + lx);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 2D step, z-march.  Each warp owns a 128-column strip of TZ consecutive rows
 // of one shot (a CTA stacks NW such warps in z) and walks down it: lane l
 // keeps the 9-row z window of its 4 columns in registers, takes its x
@@ -991,11 +1172,14 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {1, 16, 2, 4, 0}, {1, 32, 2, 3, 0}, {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4},
                                    {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2}, {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0},
                                    {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0}, {1, 32, 1, 3, 0}, {2, 16, 8, 0, 8},
-                                   {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}};
+                                   {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}, {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4},
+                                   {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2}, {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
-                                   {1, 16, 1, 4, 0}, {2, 16, 8, 0, 8}, {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}};
+                                   {1, 16, 1, 4, 0}, {2, 16, 8, 0, 8}, {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8},
+                                   {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
+                                   {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}};
 static int g_selected[2] = {-1, -1};
 static const int kDefault2D[2] = {9, 7};
 
@@ -1039,6 +1223,19 @@ static void launch_2d_group(const StepArgs& a, cudaStream_t s)
     k_step2d_sg<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(a);
 }
 
+template <int TZ, int BZ, int G, bool ADJ>
+static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+{
+    constexpr size_t smem = (size_t)(2 * (TZ + 8) * (kTX + 8) + (ADJ ? TZ * kTX : 0)) * 4 + 128;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
+    k_step2d_sgt<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
+}
+
 template <int TZ, int NW, int D, bool ADJ>
 static void launch_2d_march(const StepArgs& a, cudaStream_t s)
 {
@@ -1076,6 +1273,12 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 15: launch_2d_group<16, 8, 8, false>(a, s); break;
             case 16: launch_2d_group<16, 8, 16, false>(a, s); break;
             case 17: launch_2d_group<8, 8, 8, false>(a, s); break;
+            case 18: launch_2d_group_tma<16, 8, 2, false>(a, maps, s); break;
+            case 19: launch_2d_group_tma<16, 8, 4, false>(a, maps, s); break;
+            case 20: launch_2d_group_tma<16, 8, 8, false>(a, maps, s); break;
+            case 21: launch_2d_group_tma<32, 8, 2, false>(a, maps, s); break;
+            case 22: launch_2d_group_tma<32, 8, 4, false>(a, maps, s); break;
+            case 23: launch_2d_group_tma<8, 8, 4, false>(a, maps, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -1095,6 +1298,12 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 13: launch_2d_group<16, 8, 8, true>(a, s); break;
             case 14: launch_2d_group<16, 8, 16, true>(a, s); break;
             case 15: launch_2d_group<8, 8, 8, true>(a, s); break;
+            case 16: launch_2d_group_tma<16, 8, 2, true>(a, maps, s); break;
+            case 17: launch_2d_group_tma<16, 8, 4, true>(a, maps, s); break;
+            case 18: launch_2d_group_tma<16, 8, 8, true>(a, maps, s); break;
+            case 19: launch_2d_group_tma<32, 8, 2, true>(a, maps, s); break;
+            case 20: launch_2d_group_tma<32, 8, 4, true>(a, maps, s); break;
+            case 21: launch_2d_group_tma<8, 8, 4, true>(a, maps, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }

@@ -75,7 +75,7 @@ int gradient_accumulators(const Tiling& t, int ndim, int nshot)
 {
     if (ndim != 2) return nshot;
     const Variant2D v = variant_info(1, t.va);
-    return v.kind == 2 ? (nshot + v.G - 1) / v.G : nshot;
+    return v.kind == 2 || v.kind == 4 ? (nshot + v.G - 1) / v.G : nshot;
 }
 
 // Interpolation taps of one point: bilinear (2D) / trilinear (3D) weights on
