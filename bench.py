@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=4000)
     ap.add_argument("--only-main", action="store_true", help="timed gradient steps only (for launch lists)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--variants", default=None,
+                    help="FWD,ADJ 2D kernel variants to use instead of running the autotuner")
     return ap.parse_args()
 
 
@@ -276,7 +278,14 @@ def main():
     wavelet = q1[None, :, None].repeat(p.nshot, 1, 1).contiguous()
     d_obs = wave.wave_forward(grid, vel_true, p.src, wavelet, p.rec)
     store = wave.STORE_CHECKPOINT
-    tuned = wave.wave_autotune(grid, vel, p.src, wavelet, p.rec, steps=40)
+    if args.variants:
+        tuned = tuple(int(x) for x in args.variants.split(","))
+        wave.wave_set_variant(0, tuned[0])
+        wave.wave_set_variant(1, tuned[1])
+        chosen_by = "--variants"
+    else:
+        tuned = wave.wave_autotune(grid, vel, p.src, wavelet, p.rec, steps=40)
+        chosen_by = "wave_autotune"
     nbytes = wave.wave_workspace_size(grid, wave.OP_GRADIENT, p.src, p.rec, store, args.nsnap)
     work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     grad = torch.empty(grid.phys_shape, dtype=torch.float32, device=dev)
@@ -349,7 +358,7 @@ def main():
             "config": {"workload": WORKLOAD, "nshot_per_gpu": p.nshot, "nt": p.nt, "grid": f"{p.nx}x{p.nz}",
                        "padded_points": N, "store": "checkpoint", "nsnap": args.nsnap,
                        "forward_steps_per_gradient": sched_steps,
-                       "kernel_variants": {"forward": tuned[0], "adjoint": tuned[1], "chosen_by": "wave_autotune"},
+                       "kernel_variants": {"forward": tuned[0], "adjoint": tuned[1], "chosen_by": chosen_by},
                        "l2": "inputs larger than L2 (d_obs %.0f MB, checkpoints %.1f GB per GPU)" % (
                            d_obs.numel() * 4 / 1e6, nbytes / 1e9),
                        "parallelism": f"shots x{world}, gradient all-reduce" if world > 1 else "single GPU"},

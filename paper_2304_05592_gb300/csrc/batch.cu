@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(32 * kBBZ, 2)
                 const float4 C = *reinterpret_cast<const float4*>(row + 8);
                 const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
                 float lap[4];
-                lap4(w, [&](int k, float4& U, float4& D) {
-                    U = *reinterpret_cast<const float4*>(&s[r + 4 - k][lx + 4]);
-                    D = *reinterpret_cast<const float4*>(&s[r + 4 + k][lx + 4]);
+                lap4(w, [&](int k, float4& Up, float4& Dn) {
+                    Up = *reinterpret_cast<const float4*>(&s[r + 4 - k][lx + 4]);
+                    Dn = *reinterpret_cast<const float4*>(&s[r + 4 + k][lx + 4]);
                 }, lap);
                 const float4 kp = __ldg(reinterpret_cast<const float4*>(p.kap + off));
                 const float4 uo = ldcg4(un + off);

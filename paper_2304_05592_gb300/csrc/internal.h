@@ -144,14 +144,16 @@ constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile h
 // (kind 1) with tile height TZ, R rows per warp and NST stages, shot groups
 // (kind 2): one CTA runs its tile for G shots (R = thread rows), the
 // z-march (kind 3): one warp per TZ-row strip, R warps per CTA, prefetch
-// distance NST rows, or shot groups fed by TMA (kind 4, fields as kind 2).
+// distance NST rows, shot groups fed by TMA (kind 4, fields as kind 2), or
+// the persistent kernel over (tile, shot) items (kind 5, R = thread rows).
 // With kinds 2 and 4 in the adjoint, the gradient buffer holds one
-// accumulator per shot group.
+// accumulator per shot group; with kind 5, one per CTA segment of a tile.
 struct Variant2D {
     int kind, TZ, R, NST, G;
 };
 // Number of per-shot/per-group gradient accumulators the adjoint step fills.
 int gradient_accumulators(const struct Tiling& t, int ndim, int nshot);
+int persistent_slots(int v, int ncx, int ntz, int nshot);  // adjoint variant v of kind 5
 int variant_count(int which);             // which: 0 forward, 1 adjoint
 Variant2D variant_info(int which, int v);
 int current_variant(int which);           // the selected or default variant

@@ -309,9 +309,9 @@ __global__ void __launch_bounds__(32 * BZ, 1024 / (32 * BZ)) k_step2d(const Step
         const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
         const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
         float lap[4];
-        lap4(w, [&](int k, float4& U, float4& D) {
-            U = lds4(&s[r + 4 - k][lx + 4]);
-            D = lds4(&s[r + 4 + k][lx + 4]);
+        lap4(w, [&](int k, float4& Up, float4& Dn) {
+            Up = lds4(&s[r + 4 - k][lx + 4]);
+            Dn = lds4(&s[r + 4 + k][lx + 4]);
         }, lap);
         const long long off = (long long)gz * a.P + gx;
         const int dz = sponge_depth(gz, a.nb, a.nz);
@@ -469,9 +469,9 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
             const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
             const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
-            lap4(w, [&](int k, float4& U, float4& D) {
-                U = lds4(&s[cur][r + 4 - k][lx + 4]);
-                D = lds4(&s[cur][r + 4 + k][lx + 4]);
+            lap4(w, [&](int k, float4& Up, float4& Dn) {
+                Up = lds4(&s[cur][r + 4 - k][lx + 4]);
+                Dn = lds4(&s[cur][r + 4 + k][lx + 4]);
             }, lap);
             float out[4], cen[4], um[4], kv[4];
             const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -627,9 +627,9 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
             const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
             const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
-            lap4(w, [&](int k, float4& U, float4& D) {
-                U = lds4(row + 4 - k * SW);
-                D = lds4(row + 4 + k * SW);
+            lap4(w, [&](int k, float4& Up, float4& Dn) {
+                Up = lds4(row + 4 - k * SW);
+                Dn = lds4(row + 4 + k * SW);
             }, lap);
             const float cen[4] = {B.x, B.y, B.z, B.w};
             const float um[4] = {uo[rr].x, uo[rr].y, uo[rr].z, uo[rr].w};
@@ -697,6 +697,221 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
             if (live[rr])
                 *reinterpret_cast<float4*>(gq + off[rr]) = *reinterpret_cast<const float4*>(sg + r * kTX + lx);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D step, persistent over (tile, shot) items.  The items of a step, taken
+// tile-major, are split into gridDim.x contiguous ranges, one per CTA, with as
+// many CTAs as fit on the GPU at once.  A CTA therefore keeps one tile for
+// several consecutive shots: the model, the sponge factors and, in the
+// adjoint, the gradient tile are set up when its tile changes rather than per
+// shot.  Each item's halo tile of u and its tile of the previous level arrive
+// by TMA into a two-stage ring; the next item's copies are issued as soon as
+// every thread is done with the stage they overwrite, one block barrier per
+// item.  The adjoint sums the imaging term of the CTA's shots of one tile in
+// shared memory and writes it to accumulator slot (CTA - first CTA of the
+// tile): each slot has a single writer, so the gradient is deterministic.
+__host__ __device__ inline int pst_owner(long long j, int C, long long W)
+{
+    return (int)(((j + 1) * C - 1) / W);  // the CTA whose range holds item j
+}
+
+template <int TZ, int BZ, bool ADJ>
+__global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ))
+    k_step2d_pst(const __grid_constant__ StepMaps mp, const StepArgs a)
+{
+    constexpr int SW = kTX + 8;
+    constexpr int RB = TZ / BZ;
+    constexpr int SU = (TZ + 8) * SW;  // halo tile of u
+    constexpr int ST = TZ * kTX;       // tile of the previous level
+    constexpr int STAGE = SU + ST;
+    static_assert(SU % 32 == 0 && ST % 32 == 0, "sub-buffers must stay 128-byte aligned");
+    extern __shared__ unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar[2];
+    float* st = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
+    float* sg = st + 2 * STAGE;  // [TZ][kTX] gradient tile (adjoint with imaging)
+    const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
+    const CUtensorMap* mt = ADJ ? &mp.tile_a : &mp.tile_f;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int lx = 4 * tx;
+    const int ntz = (a.Nz + TZ - 1) / TZ;
+    const long long W = (long long)ntz * a.ncx * a.nshot;
+    const int C = gridDim.x;
+    const int j0 = (int)((long long)blockIdx.x * W / C), j1 = (int)((long long)(blockIdx.x + 1) * W / C);
+    if (j0 >= j1) return;  // CTA-uniform, before any barrier or copy
+    const bool imaging = ADJ && a.gacc != nullptr;
+    const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
+    constexpr uint32_t kBytes = STAGE * 4u;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int stage, int j) {
+        const int tile = j / a.nshot, shot = j - tile * a.nshot;
+        const int tz = tile / a.ncx, txi = tile - tz * a.ncx;
+        float* d = st + stage * STAGE;
+        mbar_expect_tx(&bar[stage], kBytes);
+        tma_load_4d(d, mh, &bar[stage], txi * kTX - 4, tz * TZ - 4, shot, a.u_buf);
+        tma_load_4d(d + SU, mt, &bar[stage], txi * kTX, tz * TZ, shot, a.prev_buf);
+    };
+    if (tid == 0) issue(0, j0);
+
+    int cur_tile = -1, x0 = 0, z0 = 0, nvalid = 0;
+    int off[RB];
+    bool live[RB], pad[RB];
+    float4 kp[RB];
+    float eps[RB][4], inv[RB][4];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+        off[rr] = 0;
+        live[rr] = pad[rr] = false;
+    }
+    float* gq = nullptr;
+    auto flush = [&]() {
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+            if (live[rr])
+                *reinterpret_cast<float4*>(gq + off[rr]) =
+                    *reinterpret_cast<const float4*>(sg + (ty + rr * BZ) * kTX + lx);
+    };
+
+    for (int j = j0; j < j1; ++j) {
+        const int i = j - j0, stage = i & 1;
+        const int tile = j / a.nshot, shot = j - tile * a.nshot;
+        const bool ok = mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
+        // also: every thread is done with item j-1 (its stage and its sparse phase)
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(a.err, kErrTimeout);
+                mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);  // let the copy land first
+            }
+            return;
+        }
+        if (tid == 0 && j + 1 < j1) {
+            fence_proxy_async();
+            issue(stage ^ 1, j + 1);
+        }
+        if (tile != cur_tile) {
+            if (imaging && cur_tile >= 0) flush();
+            cur_tile = tile;
+            const int tz = tile / a.ncx, txi = tile - tz * a.ncx;
+            x0 = txi * kTX;
+            z0 = tz * TZ;
+            const int gx = x0 + lx;
+            nvalid = min(4, a.Nx - gx);
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) {
+                const int gz = z0 + ty + rr * BZ;
+                off[rr] = gz * a.P + gx;
+                live[rr] = gz < a.Nz && nvalid > 0;
+                pad[rr] = gz < a.Nz && nvalid <= 0 && gx < a.P;
+                kp[rr] = live[rr] ? ld4(a.kap + off[rr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int dz = sponge_depth(gz, a.nb, a.nz);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
+                    eps[rr][e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
+                    inv[rr][e] = __frcp_rn(1.0f + eps[rr][e]);
+                }
+            }
+            if (imaging) {
+                const int slot = (int)blockIdx.x - pst_owner((long long)tile * a.nshot, C, W);
+                gq = a.gacc + (size_t)slot * a.cell;
+#pragma unroll
+                for (int rr = 0; rr < RB; ++rr) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (live[rr]) v = *reinterpret_cast<const float4*>(gq + off[rr]);
+                    *reinterpret_cast<float4*>(sg + (ty + rr * BZ) * kTX + lx) = v;
+                }
+            }
+        }
+        const size_t so = (size_t)shot * a.cell;
+        const float* sb = st + stage * STAGE;
+        const float* sp = sb + SU;
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const int r = ty + rr * BZ;
+            float* un = a.unew + so + off[rr];
+            if (!live[rr]) {
+                if (pad[rr]) *reinterpret_cast<float4*>(un) = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            const float* row = sb + (r + 4) * SW + lx;
+            const float4 A = lds4(row), B = lds4(row + 4), Cc = lds4(row + 8);
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, Cc.x, Cc.y, Cc.z, Cc.w};
+            float lap[4];
+            lap4(w, [&](int k, float4& Up, float4& Dn) {
+                Up = lds4(row + 4 - k * SW);
+                Dn = lds4(row + 4 + k * SW);
+            }, lap);
+            const float4 uo = lds4(sp + r * kTX + lx);
+            const float cen[4] = {B.x, B.y, B.z, B.w};
+            const float um[4] = {uo.x, uo.y, uo.z, uo.w};
+            const float kv[4] = {kp[rr].x, kp[rr].y, kp[rr].z, kp[rr].w};
+            const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+            float out[4];
+            update4(cen, um, lap, kv, eps[rr], inv[rr], zero4, out);
+            // a full float4: points past Nx stay the zero exterior
+            *reinterpret_cast<float4*>(un) = make_float4(out[0], nvalid > 1 ? out[1] : 0.0f,
+                                                         nvalid > 2 ? out[2] : 0.0f, nvalid > 3 ? out[3] : 0.0f);
+            if (!ADJ) {
+                if (a.st16) {
+                    if (nvalid == 4) {
+                        store_bf16x4(a.st16 + so + off[rr], out);
+                    } else {
+                        for (int e = 0; e < nvalid; ++e) a.st16[so + off[rr] + e] = __float2bfloat16_rn(out[e]);
+                    }
+                }
+                if (a.st32) {
+                    if (nvalid == 4) {
+                        *reinterpret_cast<float4*>(a.st32 + so + off[rr]) = make_float4(out[0], out[1], out[2], out[3]);
+                    } else {
+                        for (int e = 0; e < nvalid; ++e) a.st32[so + off[rr] + e] = out[e];
+                    }
+                }
+            } else if (imaging) {
+                float uf[4];
+                if (a.uf16) {
+                    unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off[rr]), uf);
+                } else {
+                    const float4 v = ld4(a.uf32 + so + off[rr]);
+                    uf[0] = v.x;
+                    uf[1] = v.y;
+                    uf[2] = v.z;
+                    uf[3] = v.w;
+                }
+                float* g = sg + r * kTX + lx;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) g[e] -= uf[e] * (out[e] - 2.0f * cen[e] + um[e]);
+            }
+        }
+        if (sparse) {
+            const int kcell = TZ / a.TZc;
+            const int tz = tile / a.ncx, txi = tile - tz * a.ncx;
+            const int cbase = (shot * a.ncx + txi) * a.ncz;
+            const int c0 = tz * kcell, c1 = min(c0 + kcell, a.ncz);
+            int ib = 0, ie = 0, gb = 0, ge = 0;
+            if (a.inj.cell_start) {
+                ib = a.inj.cell_start[cbase + c0];
+                ie = a.inj.cell_start[cbase + c1];
+            }
+            if (a.gat.cell_start) {
+                gb = a.gat.cell_start[cbase + c0];
+                ge = a.gat.cell_start[cbase + c1];
+            }
+            if (ib < ie || gb < ge) {  // CTA-uniform
+                __syncthreads();       // this item's points are written
+                sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * BZ, imaging ? sg : nullptr, z0, x0);
+            }
+        }
+    }
+    if (imaging) {
+        __syncthreads();
+        flush();
     }
 }
 
@@ -797,9 +1012,9 @@ __global__ void __launch_bounds__(32 * NW) k_step2d_zm(const StepArgs a)
         if (nvalid > 0) {
             const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
-            lap4(w, [&](int k, float4& U, float4& D) {
-                U = q[4 - k];
-                D = q[4 + k];
+            lap4(w, [&](int k, float4& Up, float4& Dn) {
+                Up = q[4 - k];
+                Dn = q[4 + k];
             }, lap);
             float out[4], kv[4];
             const float cen[4] = {B.x, B.y, B.z, B.w}, um[4] = {pc.x, pc.y, pc.z, pc.w};
@@ -955,9 +1170,9 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) k_step2d_tma(const __grid_co
                 const float4 B = q[4];
                 const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
                 float lap[4];
-                lap4(w, [&](int k, float4& U, float4& D) {
-                    U = q[4 - k];
-                    D = q[4 + k];
+                lap4(w, [&](int k, float4& Up, float4& Dn) {
+                    Up = q[4 - k];
+                    Dn = q[4 + k];
                 }, lap);
                 const float4 kp = lds4(sk + r * kTX + 4 * lane);
                 const float4 uo = lds4(sp + r * kTX + 4 * lane);
@@ -1173,13 +1388,15 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2}, {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0},
                                    {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0}, {1, 32, 1, 3, 0}, {2, 16, 8, 0, 8},
                                    {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}, {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4},
-                                   {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2}, {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}};
+                                   {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2}, {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4},
+                                   {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0}, {5, 32, 8, 0, 0}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
                                    {1, 16, 1, 4, 0}, {2, 16, 8, 0, 8}, {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8},
                                    {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
-                                   {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}};
+                                   {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}, {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0},
+                                   {5, 32, 8, 0, 0}};
 static int g_selected[2] = {-1, -1};
 static const int kDefault2D[2] = {9, 7};
 
@@ -1236,6 +1453,58 @@ static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStr
     k_step2d_sgt<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
 }
 
+template <int TZ, int BZ, bool ADJ>
+static size_t pst_smem()
+{
+    return (size_t)(2 * ((TZ + 8) * (kTX + 8) + TZ * kTX) + (ADJ ? TZ * kTX : 0)) * 4 + 128;
+}
+
+// CTAs of the persistent 2D kernel on the current device: as many as are
+// resident at once, at most one per item.
+template <int TZ, int BZ, bool ADJ>
+static int pst_ctas(long long items)
+{
+    static int per_sm[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (per_sm[dev] == 0) {
+        const size_t smem = pst_smem<TZ, BZ, ADJ>();
+        cudaFuncSetAttribute(k_step2d_pst<TZ, BZ, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int occ = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2d_pst<TZ, BZ, ADJ>, 32 * BZ, smem);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        per_sm[dev] = max(1, occ) * max(1, nsm);
+    }
+    return (int)std::min<long long>(items, per_sm[dev]);
+}
+
+template <int TZ, int BZ, bool ADJ>
+static void launch_2d_persistent(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+{
+    const long long W = (long long)((a.Nz + TZ - 1) / TZ) * a.ncx * a.nshot;
+    const int C = pst_ctas<TZ, BZ, ADJ>(W);
+    k_step2d_pst<TZ, BZ, ADJ><<<C, dim3(32, BZ), pst_smem<TZ, BZ, ADJ>(), s>>>(*maps, a);
+}
+
+// Gradient accumulator slots the persistent adjoint variant v fills: for each
+// tile, the number of CTAs whose item ranges cover its shots.
+int persistent_slots(int v, int ncx, int ntz, int nshot)
+{
+    const long long W = (long long)ncx * ntz * nshot;
+    int C = 0;
+    switch (v) {
+    case 22: C = pst_ctas<16, 8, true>(W); break;
+    case 23: C = pst_ctas<8, 8, true>(W); break;
+    case 24: C = pst_ctas<32, 8, true>(W); break;
+    default: return nshot;
+    }
+    int n = 1;
+    for (long long t = 0; t < (long long)ncx * ntz; ++t)
+        n = std::max(n, pst_owner((t + 1) * nshot - 1, C, W) - pst_owner(t * nshot, C, W) + 1);
+    return n;
+}
+
 template <int TZ, int NW, int D, bool ADJ>
 static void launch_2d_march(const StepArgs& a, cudaStream_t s)
 {
@@ -1279,6 +1548,9 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 21: launch_2d_group_tma<32, 8, 2, false>(a, maps, s); break;
             case 22: launch_2d_group_tma<32, 8, 4, false>(a, maps, s); break;
             case 23: launch_2d_group_tma<8, 8, 4, false>(a, maps, s); break;
+            case 24: launch_2d_persistent<16, 8, false>(a, maps, s); break;
+            case 25: launch_2d_persistent<8, 8, false>(a, maps, s); break;
+            case 26: launch_2d_persistent<32, 8, false>(a, maps, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -1304,6 +1576,9 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 19: launch_2d_group_tma<32, 8, 2, true>(a, maps, s); break;
             case 20: launch_2d_group_tma<32, 8, 4, true>(a, maps, s); break;
             case 21: launch_2d_group_tma<8, 8, 4, true>(a, maps, s); break;
+            case 22: launch_2d_persistent<16, 8, true>(a, maps, s); break;
+            case 23: launch_2d_persistent<8, 8, true>(a, maps, s); break;
+            case 24: launch_2d_persistent<32, 8, true>(a, maps, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }

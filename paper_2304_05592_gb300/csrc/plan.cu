@@ -75,6 +75,10 @@ int gradient_accumulators(const Tiling& t, int ndim, int nshot)
 {
     if (ndim != 2) return nshot;
     const Variant2D v = variant_info(1, t.va);
+    if (v.kind == 5) {
+        const int ntz = (t.ncz * t.TZc + v.TZ - 1) / v.TZ;
+        return persistent_slots(t.va, t.ncx, ntz, nshot);
+    }
     return v.kind == 2 || v.kind == 4 ? (nshot + v.G - 1) / v.G : nshot;
 }
 
