@@ -24,7 +24,6 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wave_oracle.c")
-_FNO_SRC = None
 _OUT = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT, "liboracle.so")
 
