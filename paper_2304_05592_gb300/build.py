@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwave.so")
-SOURCES = ["api.cu", "plan.cu", "kernels.cu", "profile.cu", "static_ws.cu", "batch.cu"]
+SOURCES = ["api.cu", "plan.cu", "kernels.cu", "profile.cu", "static_ws.cu", "batch.cu", "fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +31,8 @@ def _flags():
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(ROOT, "include", "wave.h"))
+    inc = os.path.join(ROOT, "include")
+    files += [os.path.join(inc, f) for f in os.listdir(inc)]
     return max(os.path.getmtime(f) for f in files)
 
 

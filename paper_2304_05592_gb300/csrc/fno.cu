@@ -1,0 +1,629 @@
+// fno.cu -- kernels of the Fourier neural operator used as a learned
+// preconditioner: twiddle tables, the truncated DFT along x and z and their
+// inverse directions, the per-mode complex channel mix and its backward, the
+// fused pointwise channel mix + spectral inverse + GELU, weight gradients, the
+// MSE loss and the Adam update.  The operations and layouts are those of
+// include/fno.h; the network is the FNO of Li et al. (2020) that the paper
+// uses as a learned surrogate (section "Fourier neural operator surrogates").
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "fno.h"
+#include "internal.h"
+
+namespace wave {
+namespace {
+
+__device__ __forceinline__ float ldf(const float* p, size_t i) { return p[i]; }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p, size_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void stf(float* p, size_t i, float v) { p[i] = v; }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, size_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+
+// GELU(x) = x Phi(x) with Phi the standard normal distribution function.
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// --- tables -------------------------------------------------------------------
+
+__global__ void k_tables(int Nz, int Nx, int mz, int mx, float* tf, float* ti, float* tb, float* ta, float* tz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < Nx * mx) {
+        const int x = i / mx, kx = i - x * mx;
+        const long long r = ((long long)kx * x) % Nx;  // exact argument reduction
+        double s, c;
+        sincospi(2.0 * (double)r / (double)Nx, &s, &c);
+        const double w = (kx == 0 ? 1.0 : 2.0) / ((double)Nz * (double)Nx);
+        tf[2 * i] = (float)c;
+        tf[2 * i + 1] = (float)(-s);
+        ti[2 * i] = (float)(w * c);
+        ti[2 * i + 1] = (float)(w * s);
+        tb[2 * i] = (float)(w * c);
+        tb[2 * i + 1] = (float)(-w * s);
+        ta[2 * i] = (float)c;
+        ta[2 * i + 1] = (float)s;
+    }
+    const int KZ = 2 * mz;
+    if (i < Nz * KZ) {
+        const int z = i / KZ, a = i - z * KZ;
+        const int kz = a < mz ? a : Nz - KZ + a;  // rows 0..mz-1, then Nz-mz..Nz-1
+        const long long r = ((long long)kz * z) % Nz;
+        double s, c;
+        sincospi(2.0 * (double)r / (double)Nz, &s, &c);
+        tz[2 * i] = (float)c;
+        tz[2 * i + 1] = (float)s;
+    }
+}
+
+// --- along x: out[r][n] = sum_x in[r][x] tab[x][n], n < 2 mx ------------------
+// CTA = 256 threads, 256 rows; thread (tr, tn) owns rows 8 tr .. 8 tr + 7 and
+// outputs 4 tn .. 4 tn + 3, accumulated over x in chunks of 32 staged in
+// shared memory (rows padded to 33 floats: conflict-free in both directions).
+constexpr int kDxRows = 256, kDxChunk = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dft_x(long long rows, int Nx, int n2, const T* __restrict__ in,
+                                               const float* __restrict__ tab, float* __restrict__ out)
+{
+    __shared__ float sv[kDxRows][kDxChunk + 1];
+    __shared__ __align__(16) float st[kDxChunk][32];
+    const int tid = threadIdx.x, tn = tid & 7, tr = tid >> 3;
+    const long long r0 = (long long)blockIdx.x * kDxRows;
+    float acc[8][4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = 0.0f;
+    for (int xc = 0; xc < Nx; xc += kDxChunk) {
+        for (int e = tid; e < kDxRows * kDxChunk; e += 256) {
+            const int row = e / kDxChunk, x = e - row * kDxChunk;
+            const long long gr = r0 + row;
+            sv[row][x] = (gr < rows && xc + x < Nx) ? ldf(in, (size_t)gr * Nx + xc + x) : 0.0f;
+        }
+        for (int e = tid; e < kDxChunk * 32; e += 256) {
+            const int x = e >> 5, n = e & 31;
+            st[x][n] = (xc + x < Nx && n < n2) ? tab[(size_t)(xc + x) * n2 + n] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int x = 0; x < kDxChunk; ++x) {
+            const float4 t = *reinterpret_cast<const float4*>(&st[x][4 * tn]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float a = sv[8 * tr + q][x];
+                acc[q][0] = fmaf(a, t.x, acc[q][0]);
+                acc[q][1] = fmaf(a, t.y, acc[q][1]);
+                acc[q][2] = fmaf(a, t.z, acc[q][2]);
+                acc[q][3] = fmaf(a, t.w, acc[q][3]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long long gr = r0 + 8 * tr + q;
+        if (gr >= rows) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * tn + c < n2) out[(size_t)gr * n2 + 4 * tn + c] = acc[q][c];
+    }
+}
+
+// --- along z -------------------------------------------------------------------
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// out[b][a][kx] = sum_z in[b][z][kx] conj(E[z][a]); one CTA per b.
+__global__ void __launch_bounds__(256) k_dft_z(int Nz, int KZ, int mx, const float2* __restrict__ in,
+                                               const float2* __restrict__ tz, float2* __restrict__ out)
+{
+    __shared__ float2 si[32][16];
+    __shared__ float2 se[32][64];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int nout = KZ * mx;
+    float2 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int z0 = 0; z0 < Nz; z0 += 32) {
+        const int zc = min(32, Nz - z0);
+        for (int e = tid; e < 32 * mx; e += 256) {
+            const int zz = e / mx, kx = e - zz * mx;
+            si[zz][kx] = zz < zc ? in[((size_t)b * Nz + z0 + zz) * mx + kx] : make_float2(0.f, 0.f);
+        }
+        for (int e = tid; e < 32 * KZ; e += 256) {
+            const int zz = e / KZ, a = e - zz * KZ;
+            se[zz][a] = zz < zc ? tz[(size_t)(z0 + zz) * KZ + a] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int o = tid + 256 * q;
+            if (o >= nout) continue;
+            const int a = o / mx, kx = o - a * mx;
+            for (int zz = 0; zz < zc; ++zz) acc[q] = cadd(acc[q], cmulc(si[zz][kx], se[zz][a]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = tid + 256 * q;
+        if (o < nout) out[(size_t)b * nout + o] = acc[q];
+    }
+}
+
+// out[b][z][kx] = sum_a in[b][a][kx] E[z][a]; CTA per (b, 32 rows of z).
+__global__ void __launch_bounds__(256) k_idft_z(int Nz, int KZ, int mx, const float2* __restrict__ in,
+                                                const float2* __restrict__ tz, float2* __restrict__ out)
+{
+    __shared__ float2 sx[64][16];
+    __shared__ float2 se[32][64];
+    const int b = blockIdx.x, z0 = blockIdx.y * 32, tid = threadIdx.x;
+    for (int e = tid; e < KZ * mx; e += 256) sx[e / mx][e % mx] = in[(size_t)b * KZ * mx + e];
+    for (int e = tid; e < 32 * KZ; e += 256) {
+        const int zz = e / KZ, a = e - zz * KZ;
+        se[zz][a] = z0 + zz < Nz ? tz[(size_t)(z0 + zz) * KZ + a] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int o = tid; o < 32 * mx; o += 256) {
+        const int zz = o / mx, kx = o - zz * mx;
+        if (z0 + zz >= Nz) continue;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int a = 0; a < KZ; ++a) acc = cadd(acc, cmul(sx[a][kx], se[zz][a]));
+        out[((size_t)b * Nz + z0 + zz) * mx + kx] = acc;
+    }
+}
+
+// --- per-mode channel mix ---------------------------------------------------------
+
+__global__ void k_mix(int B, int Ci, int Co, int nm, const float2* __restrict__ X, const float2* __restrict__ R,
+                      float2* __restrict__ Y)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * Co * nm) return;
+    const int m = (int)(t % nm);
+    const long long bo = t / nm;
+    const int o = (int)(bo % Co), b = (int)(bo / Co);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = 0; i < Ci; ++i)
+        acc = cadd(acc, cmul(X[((size_t)b * Ci + i) * nm + m], R[((size_t)i * Co + o) * nm + m]));
+    Y[t] = acc;
+}
+
+__global__ void k_mix_dx(int B, int Ci, int Co, int nm, const float2* __restrict__ dY, const float2* __restrict__ R,
+                         float2* __restrict__ dX)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * Ci * nm) return;
+    const int m = (int)(t % nm);
+    const long long bi = t / nm;
+    const int i = (int)(bi % Ci), b = (int)(bi / Ci);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int o = 0; o < Co; ++o)
+        acc = cadd(acc, cmulc(dY[((size_t)b * Co + o) * nm + m], R[((size_t)i * Co + o) * nm + m]));
+    dX[t] = acc;
+}
+
+__global__ void k_mix_dr(int B, int Ci, int Co, int nm, const float2* __restrict__ X, const float2* __restrict__ dY,
+                         float2* __restrict__ dR)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)Ci * Co * nm) return;
+    const int m = (int)(t % nm);
+    const long long io = t / nm;
+    const int o = (int)(io % Co), i = (int)(io / Co);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < B; ++b)  // conj(X) dY, summed over the batch in order
+        acc = cadd(acc, cmulc(dY[((size_t)b * Co + o) * nm + m], X[((size_t)b * Ci + i) * nm + m]));
+    dR[t] = acc;
+}
+
+// --- fused pointwise mix + spectral inverse + activation ------------------------------
+// CTA = 256 pixels of one (b, z) row; M (padded to CIMAX per row), bias and the
+// row's spectral coefficients T[b][o][z][:] are staged in shared memory and read
+// as broadcasts; each thread keeps its pixel's ci inputs and the 2 mx table
+// factors of its x in registers and produces all co outputs.
+template <int CIMAX, typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx, int mx, const Tin* __restrict__ in,
+                                                 const float* __restrict__ M, int mtrans,
+                                                 const float* __restrict__ bias, const float* __restrict__ T,
+                                                 const float* __restrict__ tab, int act, float* __restrict__ pre,
+                                                 Tout* __restrict__ out)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* sM = sm;                  // [co][CIMAX]
+    float* sT = sM + co * CIMAX;     // [co][32]
+    float* sB = sT + co * 32;        // [co]
+    const int b = blockIdx.z, z = blockIdx.y, tid = threadIdx.x;
+    const int x = blockIdx.x * 256 + tid;
+    const int n2 = 2 * mx;
+    for (int e = tid; e < co * CIMAX; e += 256) {
+        const int o = e / CIMAX, i = e - o * CIMAX;
+        sM[e] = i < ci ? (mtrans ? M[(size_t)i * co + o] : M[(size_t)o * ci + i]) : 0.0f;
+    }
+    for (int e = tid; e < co * 32; e += 256) {
+        const int o = e >> 5, r = e & 31;
+        sT[e] = (T && r < n2) ? T[(((size_t)b * co + o) * Nz + z) * n2 + r] : 0.0f;
+    }
+    for (int e = tid; e < co; e += 256) sB[e] = bias ? bias[e] : 0.0f;
+    __syncthreads();
+    if (x >= Nx) return;  // no barrier follows
+    const size_t npix = (size_t)Nz * Nx, pix = (size_t)z * Nx + x;
+    float v[CIMAX];
+#pragma unroll
+    for (int i = 0; i < CIMAX; ++i) v[i] = i < ci ? ldf(in, ((size_t)b * ci + i) * npix + pix) : 0.0f;
+    float tc[16], ts[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        tc[k] = (T && k < mx) ? tab[((size_t)x * mx + k) * 2] : 0.0f;
+        ts[k] = (T && k < mx) ? tab[((size_t)x * mx + k) * 2 + 1] : 0.0f;
+    }
+    for (int o = 0; o < co; ++o) {
+        float acc = sB[o];
+        const float* mr = sM + o * CIMAX;
+#pragma unroll
+        for (int i = 0; i < CIMAX; ++i) acc = fmaf(mr[i], v[i], acc);
+        const float* tr = sT + o * 32;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            acc = fmaf(tr[2 * k], tc[k], acc);
+            acc = fmaf(-tr[2 * k + 1], ts[k], acc);
+        }
+        const size_t oi = ((size_t)b * co + o) * npix + pix;
+        if (pre) pre[oi] = acc;
+        stf(out, oi, act == FNO_ACT_GELU ? gelu(acc) : acc);
+    }
+}
+
+// --- weight gradients ---------------------------------------------------------------
+// Block k sums its pixel range into partial[k][o][0..cip) (column ci is the
+// bias, fed by a constant 1); k_wgrad_reduce adds the blocks in index order.
+constexpr int kWgPx = 32, kWgChunk = 2048;
+
+__host__ __device__ inline int wg_cip(int ci) { return ((ci + 1) + 3) & ~3; }
+inline long long wg_blocks(int B, long long npix) { return (B * npix + kWgChunk - 1) / kWgChunk; }
+
+__global__ void k_wgrad(int B, int ci, int co, long long npix, const float* __restrict__ dU,
+                        const float* __restrict__ in, float* __restrict__ partial)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int cip = wg_cip(ci), g4 = cip / 4;
+    float* sD = sm;                       // [kWgPx][co + 1]
+    float* sI = sm + kWgPx * (co + 1);    // [kWgPx][cip]
+    const long long total = (long long)B * npix;
+    const long long g0 = (long long)blockIdx.x * kWgChunk, g1 = min(g0 + kWgChunk, total);
+    const int tid = threadIdx.x, ntask = co * g4;
+    // up to two (o, 4 i) tasks per thread
+    float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    for (long long g = g0; g < g1; g += kWgPx) {
+        for (int e = tid; e < kWgPx * co; e += blockDim.x) {
+            const int oo = e / kWgPx, p = e - oo * kWgPx;
+            float val = 0.0f;
+            if (g + p < g1) {
+                const long long bb = (g + p) / npix, pp = (g + p) - bb * npix;
+                val = dU[((size_t)bb * co + oo) * npix + pp];
+            }
+            sD[p * (co + 1) + oo] = val;
+        }
+        for (int e = tid; e < kWgPx * cip; e += blockDim.x) {
+            const int ii = e / kWgPx, p = e - ii * kWgPx;
+            float val = 0.0f;
+            if (g + p < g1) {
+                if (ii < ci) {
+                    const long long bb = (g + p) / npix, pp = (g + p) - bb * npix;
+                    val = in[((size_t)bb * ci + ii) * npix + pp];
+                } else if (ii == ci) {
+                    val = 1.0f;
+                }
+            }
+            sI[p * cip + ii] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int task = tid + q * (int)blockDim.x;
+            if (task >= ntask) continue;
+            const int o = task / g4, i4 = task - o * g4;
+#pragma unroll 8
+            for (int p = 0; p < kWgPx; ++p) {
+                const float d = sD[p * (co + 1) + o];
+                const float4 a = *reinterpret_cast<const float4*>(&sI[p * cip + 4 * i4]);
+                acc[q].x = fmaf(d, a.x, acc[q].x);
+                acc[q].y = fmaf(d, a.y, acc[q].y);
+                acc[q].z = fmaf(d, a.z, acc[q].z);
+                acc[q].w = fmaf(d, a.w, acc[q].w);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int task = tid + q * (int)blockDim.x;
+        if (task >= ntask) continue;
+        const int o = task / g4, i4 = task - o * g4;
+        *reinterpret_cast<float4*>(&partial[((size_t)blockIdx.x * co + o) * cip + 4 * i4]) = acc[q];
+    }
+}
+
+__global__ void k_wgrad_reduce(int ci, int co, long long nblk, const float* __restrict__ partial,
+                               float* __restrict__ dM, float* __restrict__ dbias)
+{
+    const int cip = wg_cip(ci);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= co * (ci + 1)) return;
+    const int o = t / (ci + 1), i = t - o * (ci + 1);
+    float s = 0.0f;
+    for (long long k = 0; k < nblk; ++k) s += partial[((size_t)k * co + o) * cip + i];
+    if (i < ci) dM[(size_t)o * ci + i] = s;
+    else if (dbias) dbias[o] = s;
+}
+
+// --- elementwise ------------------------------------------------------------------------
+
+__global__ void k_gelu_bwd(long long n, const float* __restrict__ dout, const float* __restrict__ pre,
+                           float* __restrict__ dpre)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dpre[i] = dout[i] * gelu_grad(pre[i]);
+}
+
+constexpr int kMseBlocks = 256;
+
+__global__ void __launch_bounds__(256) k_mse(long long n, const float* __restrict__ pred,
+                                             const float* __restrict__ target, float* __restrict__ dpred,
+                                             double* __restrict__ part)
+{
+    __shared__ double s[256];
+    double acc = 0.0;
+    const float scale = (float)(2.0 / (double)n);
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x) {
+        const float r = pred[i] - target[i];
+        acc += (double)r * (double)r;
+        if (dpred) dpred[i] = scale * r;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_mse_final(long long n, const double* __restrict__ part, double* __restrict__ loss)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int k = 0; k < kMseBlocks; ++k) s += part[k];
+    *loss = s / (double)n;
+}
+
+// omb1 = 1 - b1 and omb2 = 1 - b2 are formed in double and then rounded: 1 - b2
+// formed in float from b2 = 0.999f would be off by 1.3e-5 relative.
+__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float omb1, float omb2, float eps, float c1,
+                       float c2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + omb1 * gi;
+        const float vi = b2 * v[i] + omb2 * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+wave_status_t launched()
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return WAVE_ERR_CUDA;
+    }
+    return WAVE_OK;
+}
+
+bool modes_ok(int Nz, int Nx, int mz, int mx)
+{
+    return Nz > 0 && Nx > 0 && mz >= 1 && mz <= 32 && 2 * mz <= Nz && mx >= 1 && mx <= 16 && 2 * mx <= Nx;
+}
+
+template <int CIMAX, typename Tin, typename Tout>
+void combine_launch(int B, int ci, int co, int Nz, int Nx, int mx, const void* in, const float* M, int mt,
+                    const float* bias, const float* T, const float* tab, int act, float* pre, void* out,
+                    cudaStream_t s)
+{
+    const size_t smem = (size_t)(co * CIMAX + co * 32 + co) * sizeof(float);
+    dim3 grid((Nx + 255) / 256, Nz, B);
+    k_combine<CIMAX, Tin, Tout><<<grid, 256, smem, s>>>(ci, co, Nz, Nx, mx, static_cast<const Tin*>(in), M, mt, bias,
+                                                         T, tab, act, pre, static_cast<Tout*>(out));
+}
+
+template <typename Tin, typename Tout>
+void combine_dispatch(int B, int ci, int co, int Nz, int Nx, int mx, const void* in, const float* M, int mt,
+                      const float* bias, const float* T, const float* tab, int act, float* pre, void* out,
+                      cudaStream_t s)
+{
+    if (ci <= 4) combine_launch<4, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
+    else if (ci <= 8) combine_launch<8, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
+    else if (ci <= 16) combine_launch<16, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
+    else if (ci <= 32) combine_launch<32, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
+    else combine_launch<64, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
+}
+
+}  // namespace
+}  // namespace wave
+
+using namespace wave;
+
+extern "C" {
+
+wave_status_t fno_tables(int Nz, int Nx, int mz, int mx, float* tx_fwd, float* tx_inv, float* tx_bwd, float* tx_adj,
+                         float* tz, void* stream)
+{
+    if (!modes_ok(Nz, Nx, mz, mx) || !tx_fwd || !tx_inv || !tx_bwd || !tx_adj || !tz) return WAVE_ERR_ARG;
+    const int n = max(Nx * mx, Nz * 2 * mz);
+    k_tables<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(Nz, Nx, mz, mx, tx_fwd, tx_inv, tx_bwd, tx_adj, tz);
+    return launched();
+}
+
+wave_status_t fno_dft_x(long long rows, int Nx, int mx, const void* in, int in_bf16, const float* table, float* out,
+                        void* stream)
+{
+    if (rows < 0 || Nx <= 0 || mx < 1 || mx > 16 || !in || !table || !out) return WAVE_ERR_ARG;
+    if (rows == 0) return WAVE_OK;
+    const long long nblk = (rows + kDxRows - 1) / kDxRows;
+    if (nblk > 0x7fffffffLL) return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (in_bf16)
+        k_dft_x<__nv_bfloat16><<<(unsigned)nblk, 256, 0, s>>>(rows, Nx, 2 * mx, static_cast<const __nv_bfloat16*>(in),
+                                                              table, out);
+    else
+        k_dft_x<float><<<(unsigned)nblk, 256, 0, s>>>(rows, Nx, 2 * mx, static_cast<const float*>(in), table, out);
+    return launched();
+}
+
+wave_status_t fno_dft_z(int nb, int Nz, int mz, int mx, const float* in, const float* tz, float* out, void* stream)
+{
+    if (nb < 0 || !modes_ok(Nz, 2 * mx, mz, mx) || !in || !tz || !out) return WAVE_ERR_ARG;
+    if (nb == 0) return WAVE_OK;
+    k_dft_z<<<nb, 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
+                                                  reinterpret_cast<const float2*>(tz), reinterpret_cast<float2*>(out));
+    return launched();
+}
+
+wave_status_t fno_idft_z(int nb, int Nz, int mz, int mx, const float* in, const float* tz, float* out, void* stream)
+{
+    if (nb < 0 || !modes_ok(Nz, 2 * mx, mz, mx) || !in || !tz || !out) return WAVE_ERR_ARG;
+    if (nb == 0) return WAVE_OK;
+    dim3 grid(nb, (Nz + 31) / 32);
+    k_idft_z<<<grid, 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
+                                                     reinterpret_cast<const float2*>(tz),
+                                                     reinterpret_cast<float2*>(out));
+    return launched();
+}
+
+wave_status_t fno_mix(int B, int Ci, int Co, int nmode, const float* X, const float* R, float* Y, void* stream)
+{
+    if (B < 0 || Ci < 1 || Co < 1 || Ci > 64 || Co > 64 || nmode < 1 || !X || !R || !Y) return WAVE_ERR_ARG;
+    const long long n = (long long)B * Co * nmode;
+    if (n == 0) return WAVE_OK;
+    k_mix<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        B, Ci, Co, nmode, reinterpret_cast<const float2*>(X), reinterpret_cast<const float2*>(R),
+        reinterpret_cast<float2*>(Y));
+    return launched();
+}
+
+wave_status_t fno_mix_backward(int B, int Ci, int Co, int nmode, const float* X, const float* R, const float* dY,
+                               float* dX, float* dR, void* stream)
+{
+    if (B < 0 || Ci < 1 || Co < 1 || Ci > 64 || Co > 64 || nmode < 1 || !dY) return WAVE_ERR_ARG;
+    if ((dX && !R) || (dR && !X)) return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dX && B > 0) {
+        const long long n = (long long)B * Ci * nmode;
+        k_mix_dx<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, Ci, Co, nmode, reinterpret_cast<const float2*>(dY),
+                                                            reinterpret_cast<const float2*>(R),
+                                                            reinterpret_cast<float2*>(dX));
+    }
+    if (dR) {
+        const long long n = (long long)Ci * Co * nmode;
+        k_mix_dr<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, Ci, Co, nmode, reinterpret_cast<const float2*>(X),
+                                                            reinterpret_cast<const float2*>(dY),
+                                                            reinterpret_cast<float2*>(dR));
+    }
+    return launched();
+}
+
+wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const void* in, int in_bf16,
+                          const float* M, int m_trans, const float* bias, const float* T, const float* table,
+                          int act, float* pre, void* out, int out_bf16, void* stream)
+{
+    if (B < 0 || Ci < 1 || Ci > 64 || Co < 1 || Co > 64 || Nz < 1 || Nx < 1 || !in || !M || !out) return WAVE_ERR_ARG;
+    if (T && (!table || mx < 1 || mx > 16)) return WAVE_ERR_ARG;
+    if (act != FNO_ACT_NONE && act != FNO_ACT_GELU) return WAVE_ERR_ARG;
+    if (B == 0) return WAVE_OK;
+    if (Nz > 65535 || B > 65535) return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int mxe = T ? mx : 1;
+    if (in_bf16 && out_bf16)
+        combine_dispatch<__nv_bfloat16, __nv_bfloat16>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre,
+                                                       out, s);
+    else if (in_bf16)
+        combine_dispatch<__nv_bfloat16, float>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre, out, s);
+    else if (out_bf16)
+        combine_dispatch<float, __nv_bfloat16>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre, out, s);
+    else
+        combine_dispatch<float, float>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre, out, s);
+    return launched();
+}
+
+size_t fno_wgrad_work_floats(int B, int Ci, int Co, long long npix)
+{
+    if (B < 0 || Ci < 1 || Co < 1 || npix < 0) return 0;
+    return (size_t)wg_blocks(B, npix) * Co * wg_cip(Ci);
+}
+
+wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, const float* in, float* dM,
+                        float* dbias, float* work, void* stream)
+{
+    if (B < 0 || Ci < 1 || Ci > 64 || Co < 1 || Co > 64 || npix < 0 || !dU || !in || !dM || !work)
+        return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nblk = wg_blocks(B, npix);
+    if (nblk > 0x7fffffffLL) return WAVE_ERR_ARG;
+    if (nblk > 0) {
+        const int ntask = Co * (wg_cip(Ci) / 4);
+        const int threads = std::min(1024, (((ntask + 1) / 2 + 31) / 32) * 32);
+        const size_t smem = (size_t)(kWgPx * (Co + 1) + kWgPx * wg_cip(Ci)) * sizeof(float);
+        k_wgrad<<<(unsigned)nblk, threads, smem, s>>>(B, Ci, Co, npix, dU, in, work);
+    }
+    const int nout = Co * (Ci + 1);
+    k_wgrad_reduce<<<(nout + 255) / 256, 256, 0, s>>>(Ci, Co, nblk, work, dM, dbias);
+    return launched();
+}
+
+wave_status_t fno_gelu_backward(long long n, const float* dout, const float* pre, float* dpre, void* stream)
+{
+    if (n < 0 || !dout || !pre || !dpre) return WAVE_ERR_ARG;
+    if (n == 0) return WAVE_OK;
+    const long long nb = std::min<long long>((n + 255) / 256, 4096);
+    k_gelu_bwd<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(n, dout, pre, dpre);
+    return launched();
+}
+
+wave_status_t fno_mse(long long n, const float* pred, const float* target, float* dpred, double* loss, double* work,
+                      void* stream)
+{
+    if (n <= 0 || !pred || !target || !loss || !work) return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_mse<<<kMseBlocks, 256, 0, s>>>(n, pred, target, dpred, work);
+    k_mse_final<<<1, 32, 0, s>>>(n, work, loss);
+    return launched();
+}
+
+wave_status_t fno_adam(long long n, float* p, const float* g, float* m, float* v, double lr, double b1, double b2,
+                       double eps, int t, void* stream)
+{
+    if (n < 0 || t < 1 || !p || !g || !m || !v) return WAVE_ERR_ARG;
+    if (n == 0) return WAVE_OK;
+    const float c1 = (float)(1.0 - pow(b1, t)), c2 = (float)(1.0 - pow(b2, t));
+    const long long nb = std::min<long long>((n + 255) / 256, 4096);
+    k_adam<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(n, p, g, m, v, (float)lr, (float)b1, (float)b2,
+                                                           (float)(1.0 - b1), (float)(1.0 - b2), (float)eps, c1, c2);
+    return launched();
+}
+
+}  // extern "C"

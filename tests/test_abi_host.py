@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI (no GPU needed): the library loads, exports
-every function that include/wave.h declares, and its host-only entry points
+every function that include/*.h declares, and its host-only entry points
 (workspace sizing, geometry validation, stability limit, checkpoint schedule)
 behave as documented."""
 import ctypes
@@ -28,13 +28,15 @@ def declared_functions():
     for h in os.listdir(os.path.join(ROOT, "include")):
         if h.endswith(".h"):
             text = open(os.path.join(ROOT, "include", h)).read()
-            names += re.findall(r"^\s*(?:wave_status_t|double|long long|int|const char\*)\s+(wave_\w+)\s*\(", text, re.M)
+            names += re.findall(r"^\s*(?:wave_status_t|double|long long|int|size_t|const char\*)\s+((?:wave|fno)_\w+)\s*\(",
+                                text, re.M)
     return sorted(set(names))
 
 
 def test_library_exports_every_declared_symbol():
     names = declared_functions()
-    assert {"wave_forward", "wave_adjoint", "wave_gradient", "wave_workspace_size"} <= set(names)
+    assert {"wave_forward", "wave_adjoint", "wave_gradient", "wave_workspace_size", "fno_combine", "fno_dft_x",
+            "fno_mix_backward", "fno_wgrad_work_floats"} <= set(names)
     lib = ctypes.CDLL(wave.library_path())
     for n in names:
         assert hasattr(lib, n), n
