@@ -230,3 +230,101 @@ def observed_noise(shape, scale: float, seed: int) -> np.ndarray:
     """Seeded Gaussian noise array (float32) used as a stand-in observed record."""
     rng = np.random.default_rng(seed)
     return _f32(scale * rng.standard_normal(shape))
+
+
+# --- plume-shaped time-lapse perturbations --------------------------------------
+
+def patchy_velocity(sw, vp, rho, phi, k_min=36.6e9, k_brine=2.735e9, k_co2=0.125e9, rho_brine=1000.0,
+                    rho_co2=700.0):
+    """P-wave velocity after a CO2 saturation sw under patchy mixing: the rock
+    physics model R of arxiv 2304.05592 (section "Putting it all together",
+    after Avseth, Mukerji and Mavko 2010).  The brine-saturated moduli come from
+    vp and vs = vp / sqrt(3); Gassmann's relation gives the bulk modulus of the
+    rock fully saturated with CO2; the patchy mixture averages the two
+    P-wave moduli harmonically with weights 1 - sw and sw; density changes by
+    phi sw (rho_co2 - rho_brine).  Returns (vp_new, rho_new)."""
+    sw, vp, rho = np.asarray(sw, float), np.asarray(vp, float), np.asarray(rho, float)
+    mu = rho * vp ** 2 / 3.0                       # shear modulus (vs^2 = vp^2 / 3)
+    k_sat = rho * vp ** 2 - 4.0 / 3.0 * mu         # brine-saturated bulk modulus
+    # Gassmann: K_sat/(K_min - K_sat) - K_fl/(phi (K_min - K_fl)) is the same
+    # for every pore fluid; swap brine for CO2
+    a = k_sat / (k_min - k_sat) - k_brine / (phi * (k_min - k_brine)) + k_co2 / (phi * (k_min - k_co2))
+    k_co2_sat = k_min * a / (1.0 + a)
+    m1, m2 = k_sat + 4.0 / 3.0 * mu, k_co2_sat + 4.0 / 3.0 * mu
+    m_mix = 1.0 / ((1.0 - sw) / m1 + sw / m2)      # P-wave modulus of the patchy mixture
+    rho_new = rho + phi * sw * (rho_co2 - rho_brine)
+    return np.sqrt(m_mix / rho_new), rho_new
+
+
+def plume_saturation(nz: int, nx: int, rng, z_cap: int, z_bot: int) -> np.ndarray:
+    """CO2 saturation in [0, 1] on [nz][nx]: an inverted cone rising from an
+    injection point at the reservoir bottom (row z_bot) to the seal (row z_cap),
+    spreading under the seal, plus one to three thin lateral lobes (stacked
+    high-permeability streaks); edges are smoothed over a few cells."""
+    z, x = np.meshgrid(np.arange(nz, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    xi = rng.uniform(0.3, 0.7) * nx
+    height = z_bot - z_cap
+    w0 = rng.uniform(0.01, 0.03) * nx
+    slope = rng.uniform(0.4, 1.2)
+    half = w0 + np.clip(z_bot - z, 0.0, None) * slope   # cone half-width, wider upwards
+    inside = (z >= z_cap) & (z <= z_bot)
+    d = np.where(inside, np.abs(x - xi) - half, np.inf)
+    s = 1.0 / (1.0 + np.exp(np.clip(d / 2.0, -50, 50)))
+    # spreading under the seal
+    t_cap = rng.uniform(0.08, 0.2) * height
+    w_cap = half.max() * rng.uniform(1.1, 1.6)
+    cap = (z >= z_cap) & (z <= z_cap + t_cap)
+    s = np.maximum(s, np.where(cap, 1.0 / (1.0 + np.exp(np.clip((np.abs(x - xi) - w_cap) / 2.0, -50, 50))), 0.0))
+    for _ in range(int(rng.integers(1, 4))):
+        zl = rng.uniform(z_cap + 0.3 * height, z_bot - 0.1 * height)
+        tl = rng.uniform(0.03, 0.08) * height
+        wl = half.max() * rng.uniform(1.0, 2.0)
+        xl = xi + rng.uniform(-0.3, 0.3) * wl
+        lobe = (np.abs(z - zl) <= tl) & inside
+        s = np.maximum(s, np.where(lobe, 1.0 / (1.0 + np.exp(np.clip((np.abs(x - xl) - wl) / 2.0, -50, 50))), 0.0))
+    return np.where(inside, s, 0.0) * rng.uniform(0.6, 1.0)
+
+
+def plume_model(seed: int, nx: int = 512, nz: int = 256, h: float = 10.0):
+    """Baseline model and plume perturbation (both float32 [nz][nx], m/s).
+
+    Baseline: 3-5 flat layers 1500-3500 m/s with a thin fast seal (2-4 % of
+    the depth) and a reservoir layer (2.8-3.3 km/s) below it.  Perturbation: the patchy
+    velocity drop of a plume-shaped saturation in the reservoir (porosity
+    0.25, density from Gardner's relation rho = 310 vp^0.25), rescaled so that
+    its largest relative drop is 2-8 %."""
+    rng = np.random.default_rng(seed)
+    base = random_layers(nx, nz, h, rng, nlayer_range=(3, 5)).astype(float)
+    z_cap = int(rng.uniform(0.45, 0.6) * nz)
+    t_seal = max(2, int(rng.uniform(0.02, 0.04) * nz))
+    z_res = z_cap + t_seal
+    z_bot = min(nz - 4, z_res + int(rng.uniform(0.15, 0.25) * nz))
+    # with vs = vp / sqrt(3) the CO2-saturated modulus stays positive for vp above ~2.7 km/s
+    v_res = rng.uniform(2800.0, 3300.0)
+    base[z_cap:z_res] = min(v_res * 1.25, 4000.0)
+    base[z_res:z_bot + 1] = v_res
+    sw = plume_saturation(nz, nx, rng, z_res, z_bot)
+    rho = 310.0 * base ** 0.25
+    vp_new, _ = patchy_velocity(sw, base, rho, 0.25)
+    dv = np.minimum(vp_new - base, 0.0)  # drops only (removes 1e-13 rounding where sw ~ 0)
+    if not np.all(np.isfinite(dv)):
+        raise ValueError("patchy substitution left the valid range")
+    drop = float(np.max(-dv / base))
+    if drop > 0:
+        dv *= rng.uniform(0.02, 0.08) / drop
+    return _f32(base), _f32(dv)
+
+
+def plume_acquisition(nx: int = 512, nz: int = 256, h: float = 10.0, nshot: int = 8, nt: int = 2000,
+                      dt: float = 0.8e-3, f0: float = 15.0, nb: int = 40, vref: float = 4000.0) -> Problem:
+    """Surface acquisition over the plume models: nshot sources at 20 m depth,
+    evenly spread, a receiver at every surface grid point (20 m depth); the
+    velocity field of the returned Problem is a placeholder (set per model)."""
+    Lx = (nx - 1) * h
+    src = np.zeros((nshot, 1, 2))
+    src[:, 0, 0] = np.linspace(0.06, 0.94, nshot) * Lx
+    src[:, 0, 1] = 2 * h
+    rec = np.stack([np.arange(nx) * h, np.full(nx, 2 * h)], axis=1)
+    rec = np.repeat(rec[None], nshot, axis=0)
+    vel = np.full((nz, nx), 2000.0, np.float32)
+    return Problem(2, nx, nz, h, dt, nt, nb, f0, vel, _f32(src), _f32(rec), vref=vref, name="plume")
