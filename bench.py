@@ -115,11 +115,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_problem(nshot: int, nt: int):
+def make_problem(nshot: int, nt: int, rank: int = 0, world: int = 1):
+    """The 32-shot gradient workload; with world > 1 ranks the survey has
+    nshot * world sources spread over the same 50-3150 m line and
+    this rank gets its contiguous shard of nshot of them."""
     from paper_2304_05592_gb300 import synth
+    from paper_2304_05592_gb300.dist import shard
 
     p = synth.config2(nshot=32, nt=nt)
-    if nshot != 32:
+    if world > 1:
+        total = nshot * world
+        xs = np.linspace(50.0, 3150.0, total)  # the 32-shot line, refined
+        mine = np.asarray(list(shard(total, rank, world)))
+        p = p.with_shots(np.zeros(len(mine), dtype=int))
+        p.src[:, 0, 0] = xs[mine]
+    elif nshot != 32:
         p = p.with_shots(np.arange(nshot) % 32)
     from scipy.ndimage import gaussian_filter
 
@@ -270,7 +280,7 @@ def main():
     from paper_2304_05592_gb300 import wave
     from paper_2304_05592_gb300.wave import Grid
 
-    p, v0 = make_problem(args.nshot, args.nt)
+    p, v0 = make_problem(args.nshot, args.nt, rank, world)
     grid = Grid.of(p)
     vel_true = torch.from_numpy(p.vel).to(dev)
     vel = torch.from_numpy(v0).to(dev)
@@ -290,11 +300,17 @@ def main():
     work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     grad = torch.empty(grid.phys_shape, dtype=torch.float32, device=dev)
 
-    def step():
+    from paper_2304_05592_gb300.dist import sharded_gradient
+
+    def grad_fn(shots):
+        # this rank's shard is fixed: p holds exactly its shots
         phi, g, _ = wave.wave_gradient(grid, vel, p.src, wavelet, p.rec, d_obs, store=store, nsnap=args.nsnap,
                                        grad=grad, work=work)
-        if world > 1:
-            dist.all_reduce(g)  # shot-summed gradient across ranks
+        return phi, g
+
+    def step():
+        # one gradient of the whole survey: this rank's shots, then one all-reduce when world > 1
+        phi, _ = sharded_gradient(grad_fn, p.nshot * world)
         return phi
 
     def barrier():
