@@ -35,8 +35,12 @@ WORKLOAD = ("2D FWI gradient, 32 shots: 512x256 at 6.25 m, layered 1500-3500 m/s
             "binomial checkpointing")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
-# the SHA-256 of the kernel source they were taken on; dropped (null) once the source changes.
-TRAFFIC = {}
+# (kernel, SHA-256 prefix of that kernel's source text plus the shared stencil header) at capture
+# time; a kernel whose source has changed since gets null.
+VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,fwd>"),
+                  (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,adj>")}
+TRAFFIC = {("k_step2d_sgt<16,8,2,fwd>", "ceb353c43c594793"): 82.16e6,
+           ("k_step2d_sgt<16,8,2,adj>", "ceb353c43c594793"): 91.16e6}
 
 
 def parse():
@@ -55,9 +59,19 @@ def parse():
     return ap.parse_args()
 
 
-def kernel_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2304_05592_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def kernel_hash(func: str) -> str:
+    """SHA-256 prefix of a kernel's definition (from its name to the closing
+    brace at column 0) in kernels.cu, plus stencil.cuh."""
+    csrc = os.path.join(ROOT, "paper_2304_05592_gb300", "csrc")
+    with open(os.path.join(csrc, "kernels.cu")) as f:
+        text = f.read()
+    i = text.find(f" {func}(")
+    if i < 0:
+        return ""
+    j = text.find("\n}\n", i)
+    with open(os.path.join(csrc, "stencil.cuh")) as f:
+        body = text[i:j] + f.read()
+    return hashlib.sha256(body.encode()).hexdigest()[:16]
 
 
 def hbm_peak():
@@ -219,6 +233,49 @@ def config3_forward(dev, peak):
             "bound": "hbm", "bytes_per_point": 16}
 
 
+def fno_preconditioner(dev):
+    """The learned preconditioner's FNO (4 Fourier layers, width 32, hidden 64,
+    16 x 16 modes on 256 x 512): FP32 training steps (forward, backward, MSE,
+    Adam) and inference with FP32 or BF16 activations, batch 8, random inputs."""
+    import torch
+
+    from paper_2304_05592_gb300 import fno
+
+    net = fno.FNO2d(fno.FNOConfig(), 256, 512, dev, seed=0)
+    B = 8
+    gen = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn((B, 3, 256, 512), generator=gen, device=dev)
+    y = torch.randn((B, 1, 256, 512), generator=gen, device=dev)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / n
+
+    t_train = timed(lambda: net.train_step(x, y, 1e-4), 10)
+    t_f32 = timed(lambda: net.forward(x, train=False), 20)
+    t_b16 = timed(lambda: net.forward(x, train=False, bf16=True), 20)
+    # algorithmic FLOPs of one forward per pixel: per layer 2 W^2 (channel mix) + 2 W 2mx (x transform)
+    # + 2 W 2mx (inverse in the fused kernel) + 16 W KZ mx Nz / (Nz Nx) (z transforms) + 8 W^2 KZ mx / (Nz Nx)
+    # (mode mix); lift 2 cin W; projection 2 W H + 2 H
+    W, H, KZ, mx, Nz, Nx, cin = 32, 64, 32, 16, 256, 512, 3
+    per_layer = 2 * W * W + 4 * W * 2 * mx + 16 * W * KZ * mx / Nx + 8 * W * W * KZ * mx / (Nz * Nx)
+    flop = (4 * per_layer + 2 * cin * W + 2 * W * H + 2 * H) * Nz * Nx
+    # FP32 CUDA-core peak from unit counts and clocks: 152 SMs x 128 FMA lanes x 2 x 2.07 GHz
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    ach = flop * B / t_f32 / 1e12
+    return {"workload": "FNO 4 layers, width 32, hidden 64, 16x16 modes, 256x512, batch 8",
+            "train_samples_per_s": B / t_train, "infer_samples_per_s_fp32": B / t_f32,
+            "infer_samples_per_s_bf16_activations": B / t_b16, "forward_gflop_per_sample": flop / 1e9,
+            "forward_roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                                 "frac": ach / alu_peak, "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}}
+
+
 def uneven_batch(dev):
     """Config 4: 64 shots of different grids, models and nt; one batched call
     (persistent sweeps, CUDA graph, BF16 store) against one call per shot."""
@@ -358,7 +415,8 @@ def main():
     dom = max(kern, key=lambda k: kern[k]["total_s"])
     kd = kern[dom]
     achieved = kd["bytes"] / kd["avg_s"] / 1e9 if kd["avg_s"] > 0 else None
-    tr = TRAFFIC.get((kd["name"], kernel_hash()))
+    vk = VARIANT_KERNEL.get((0 if dom == "fwd" else 1, tuned[0] if dom == "fwd" else tuned[1]))
+    tr = TRAFFIC.get((vk[1], kernel_hash(vk[0]))) if vk else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": tr,
                 "kernel": kd["name"], "peak_kind": peak_kind,
@@ -452,6 +510,7 @@ def main():
         line["config3_forward"] = config3_forward(dev, peak)
         torch.cuda.empty_cache()
         line["uneven_batch"] = uneven_batch(dev)
+        line["fno_preconditioner"] = fno_preconditioner(dev)
         torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p.nt)
