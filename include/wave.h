@@ -192,6 +192,17 @@ typedef struct {
     double misfit;         /* out: 1/2 ||F q - d_obs||^2 of this problem    */
 } wave_problem_t;
 
+/* The bounded wait that the persistent batch sweep uses between tiles, run by
+ * one thread on a caller-given device flag: it polls *flag >= want through L2
+ * and gives up after a fixed number of polls (a few seconds) or as soon as
+ * *abort_word is non-zero.  flag, abort_word and err are device ints owned by
+ * the caller (err is overwritten).  Synchronises the stream; returns WAVE_OK
+ * if the flag was released, WAVE_ERR_TIMEOUT if the wait gave up (the context
+ * stays usable), WAVE_ERR_ARG for a null pointer, WAVE_ERR_CUDA on a launch
+ * error.  For tests of the failure path (a flag that nothing sets); the paper
+ * has no counterpart. */
+wave_status_t wave_wait_probe(int* flag, int want, int* abort_word, int* err, void* stream);
+
 /* Workspace for wave_gradient_batch (store: WAVE_STORE_BF16 or _FP32). */
 wave_status_t wave_workspace_size_batch(const wave_problem_t* probs, int nprob, int store, size_t* bytes);
 

@@ -66,6 +66,12 @@ __device__ bool wait_flag(int* flag, int want, int* abort_word)
     return false;
 }
 
+// One thread runs the sweep's bounded wait on a caller-given flag.
+__global__ void k_wait_probe(int* flag, int want, int* abort_word, int* err)
+{
+    if (threadIdx.x == 0 && !wait_flag(flag, want, abort_word)) atomicOr(err, kErrTimeout);
+}
+
 template <bool ADJ>
 __global__ void __launch_bounds__(32 * kBBZ, 2)
     k_batch_sweep(const BProb* __restrict__ probs, const int* __restrict__ tile_prob, int ntile, int nsteps,
@@ -631,6 +637,23 @@ wave_status_t wave_gradient_batch(wave_problem_t* probs, int nprob, int store, i
     if (herr) return WAVE_ERR_CUDA;
     for (int i = 0; i < nprob; ++i) probs[i].misfit = mf[i];
     return WAVE_OK;
+}
+
+wave_status_t wave_wait_probe(int* flag, int want, int* abort_word, int* err, void* stream)
+{
+    if (!flag || !abort_word || !err) return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int herr = 0;
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return WAVE_ERR_CUDA;
+    k_wait_probe<<<1, 32, 0, s>>>(flag, want, abort_word, err);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return WAVE_ERR_CUDA;
+    }
+    return (herr & kErrTimeout) ? WAVE_ERR_TIMEOUT : WAVE_OK;
 }
 
 }  // extern "C"

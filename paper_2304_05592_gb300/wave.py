@@ -103,6 +103,8 @@ def _lib():
         lib.wave_workspace_size_batch.restype = I
         lib.wave_gradient_batch.argtypes = [ctypes.POINTER(wave_problem_t), I, I, I, I, P, ctypes.c_size_t, P]
         lib.wave_gradient_batch.restype = I
+        lib.wave_wait_probe.argtypes = [P, I, P, P, P]
+        lib.wave_wait_probe.restype = I
         lib.wave_set_variant.argtypes = [I, I]
         lib.wave_set_variant.restype = I
         lib.wave_variant_count.argtypes = [I]
@@ -469,3 +471,14 @@ def wave_workspace_size_batch(problems, store: int = STORE_BF16) -> int:
     if st:
         raise WaveError(st, "wave_workspace_size_batch")
     return int(nbytes.value)
+
+
+def wave_wait_probe(flag: torch.Tensor, want: int, abort_word: torch.Tensor, err: torch.Tensor, stream=None) -> int:
+    """Runs the batch sweep's bounded wait on device int32 scalars; returns the
+    status (0 released, 6 WAVE_ERR_TIMEOUT) instead of raising."""
+    for t, n in ((flag, "flag"), (abort_word, "abort_word"), (err, "err")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32:
+            raise TypeError(f"{n} must be a CUDA int32 tensor")
+    return int(_lib().wave_wait_probe(ctypes.c_void_p(flag.data_ptr()), int(want),
+                                      ctypes.c_void_p(abort_word.data_ptr()), ctypes.c_void_p(err.data_ptr()),
+                                      _stream(stream)))
