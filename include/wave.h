@@ -252,14 +252,17 @@ long long wave_launch_count(void);
 wave_status_t wave_profile_start(int every);
 wave_status_t wave_profile_stop(double* fwd_ms, long long* fwd_n, double* adj_ms, long long* adj_n);
 
-/* Kernel variant selection for the 2D time step (no counterpart in the
- * paper; used by the autotuner and by measurements).  which = 0 selects the
- * forward step, 1 the adjoint step; variant in [0, wave_variant_count(which))
- * or -1 for the library default.  Variant 0 is the direct-load kernel, the
- * others are TMA-pipelined persistent kernels with different tile heights and
- * stage counts; all compute the same result.  The choice is process-wide and
- * applies to calls that start after it (not thread-safe against calls in
- * flight). */
+/* Kernel variant selection for the time step (no counterpart in the paper;
+ * used by the autotuner and by measurements).  which = 0 selects the 2D
+ * forward step, 1 the 2D adjoint step, 2 the 3D step (forward and adjoint);
+ * variant in [0, wave_variant_count(which)) or -1 for the library default.
+ * 2D variants: direct loads, TMA pipeline, shot groups (cp.async or TMA fed),
+ * z-march, persistent items, with different tile shapes; 3D variants: a
+ * z-march with a shared-memory halo plane (0) and TMA plane rings with
+ * different tile heights and z chunks.  All variants of a step compute the
+ * same shot records bit for bit (one arithmetic order); gradients agree to
+ * rounding of the per-group sums.  The choice is process-wide and applies to
+ * calls that start after it (not thread-safe against calls in flight). */
 wave_status_t wave_set_variant(int which, int variant);
 int wave_variant_count(int which);
 

@@ -237,8 +237,19 @@ bool encode(CUtensorMap* m, CUtensorMapDataType type, int rank, void* ptr, const
 wave_status_t make_maps(Layout& L)
 {
     memset(&L.maps, 0, sizeof(L.maps));
-    if (L.d.ndim != 2) return WAVE_OK;
     const Dims& d = L.d;
+    if (d.ndim == 3) {
+        const Variant2D v = variant_info(2, L.t.v3);
+        if (v.kind != 6) return WAVE_OK;
+        const cuuint64_t dims[5] = {(cuuint64_t)d.Nx, (cuuint64_t)d.Ny, (cuuint64_t)d.Nz, (cuuint64_t)L.nshot,
+                                    (cuuint64_t)L.nbuf};
+        const cuuint64_t str[4] = {(cuuint64_t)d.P * 4, (cuuint64_t)d.Ny * d.P * 4, (cuuint64_t)d.cell * 4,
+                                   (cuuint64_t)L.field() * 4};
+        const cuuint32_t box[5] = {kTX + 8, (cuuint32_t)v.R + 8, 1, 1, 1};
+        return encode(&L.maps.halo3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, L.pool, dims, str, box) ? WAVE_OK
+                                                                                                : WAVE_ERR_CUDA;
+    }
+    if (d.ndim != 2) return WAVE_OK;
     const cuuint64_t fdims[4] = {(cuuint64_t)d.Nx, (cuuint64_t)d.Nz, (cuuint64_t)L.nshot, (cuuint64_t)L.nbuf};
     const cuuint64_t fstr[3] = {(cuuint64_t)d.P * 4, (cuuint64_t)d.cell * 4, (cuuint64_t)L.field() * 4};
     const cuuint64_t kdims[2] = {(cuuint64_t)d.Nx, (cuuint64_t)d.Nz};

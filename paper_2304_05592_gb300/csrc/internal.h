@@ -47,6 +47,7 @@ struct Tiling {
     int TX, TY, TZc;
     int ncx, ncy, ncz;
     int vf, va;  // 2D kernel variants for the forward / adjoint steps
+    int v3;      // 3D kernel variant
     long long cells_per_shot() const { return (long long)ncx * ncy * ncz; }
 };
 
@@ -82,6 +83,7 @@ wave_status_t build_taps(const Dims& d, const Tiling& t, int nshot, int npts, co
 // _f / _a: boxes for the forward / adjoint tile heights.
 struct StepMaps {
     CUtensorMap halo_f, tile_f, kap_f, halo_a, tile_a, kap_a, tile16_a;
+    CUtensorMap halo3;  // 3D: (x, y, z, shot, buffer) over the pool, box 136 x (TY+8) x 1 x 1 x 1
 };
 
 // Arguments of one time step of the stencil kernels.
@@ -154,7 +156,7 @@ struct Variant2D {
 // Number of per-shot/per-group gradient accumulators the adjoint step fills.
 int gradient_accumulators(const struct Tiling& t, int ndim, int nshot);
 int persistent_slots(int v, int ncx, int ntz, int nshot);  // adjoint variant v of kind 5
-int variant_count(int which);             // which: 0 forward, 1 adjoint
+int variant_count(int which);             // which: 0 2D forward, 1 2D adjoint, 2 3D
 Variant2D variant_info(int which, int v);
 int current_variant(int which);           // the selected or default variant
 int select_variant(int which, int v);     // v = -1 restores the default; 0 on success

@@ -132,6 +132,17 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, uin
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(c3), "r"(c4)
+        : "memory");
+}
+
 // 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes)
 {
@@ -1264,7 +1275,6 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
 #pragma unroll
     for (int k = 0; k < 8; ++k) q[k] = ld(z0 - 4 + k, gy, gx);
 
-    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
     for (int zz = 0; zz < TZC; ++zz) {
         const int gz = z0 + zz;
         if (gz >= a.Nz) break;
@@ -1285,20 +1295,12 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
             const float4 A = lds4(row), B = lds4(row + 4), C = lds4(row + 8);
             const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
             float lap[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                lap[i] = 3.0f * kC0 * w[i + 4] + kC1 * (w[i + 3] + w[i + 5]) + kC2 * (w[i + 2] + w[i + 6]) +
-                         kC3 * (w[i + 1] + w[i + 7]) + kC4 * (w[i] + w[i + 8]);
-#pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                const float4 U = lds4(&s[ty + 4 - k][4 * tx + 4]);
-                const float4 D = lds4(&s[ty + 4 + k][4 * tx + 4]);
-                const float4 zu = q[4 - k], zd = q[4 + k];
-                lap[0] += ck[k] * (U.x + D.x + zu.x + zd.x);
-                lap[1] += ck[k] * (U.y + D.y + zu.y + zd.y);
-                lap[2] += ck[k] * (U.z + D.z + zu.z + zd.z);
-                lap[3] += ck[k] * (U.w + D.w + zu.w + zd.w);
-            }
+            lap4_3d(w, [&](int k, float4& Up, float4& Dn, float4& Zu, float4& Zd) {
+                Up = lds4(&s[ty + 4 - k][4 * tx + 4]);
+                Dn = lds4(&s[ty + 4 + k][4 * tx + 4]);
+                Zu = q[4 - k];
+                Zd = q[4 + k];
+            }, lap);
             const long long off = gz * plane + (long long)gy * a.P + gx;
             const float4 kp = ld4(a.kap + off);
             const float4 uo = *reinterpret_cast<const float4*>(a.uprev + so + off);
@@ -1313,7 +1315,7 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
                 const float eps = kap * a.ceps * (float)(dd * dd);
                 cen[i] = w[i + 4];
                 um[i] = f4(uo, i);
-                out[i] = leap_src(cen[i], um[i], lap[i], kap, eps, bsrc[i]);
+                out[i] = leap1(cen[i], um[i], lap[i], kap, eps, __frcp_rn(1.0f + eps), bsrc[i]);
             }
             float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (imaging) {
@@ -1348,6 +1350,183 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
             ge = a.gat.cell_start[cbase + c1];
         }
         sparse_phase<ADJ>(a, ib, ie, gb, ge, so, tid, 32 * TY);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3D step fed by TMA.  Tile = 128 (x) by TY (y) points, CTA = 32 x TY threads
+// (4 x points per thread) marching over TZC planes in z.  Every xy plane of u
+// with its 4-point halo ((TY+8) x 136 floats) arrives by one 5D bulk tensor
+// load into a ring of NR = 7 shared-memory slots: planes z..z+4 are resident
+// while planes up to z+6 are in flight.  Each thread keeps the 9 planes
+// z-4..z+4 of its 4 points in registers (read once from the ring when a plane
+// arrives) and takes x and y neighbours from the centre plane's slot.  A slot
+// is refilled right after the block barrier that ends the plane that used it
+// as centre: one barrier per plane.  Sponge depths in x and y are fixed per
+// thread.  Waits are bounded; on a timeout the CTA records kErrTimeout, lets
+// its issued copies land and returns.
+constexpr int k3NR = 7;
+
+template <int TY, int TZC, bool ADJ>
+__global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const __grid_constant__ StepMaps mp,
+                                                                        const StepArgs a)
+{
+    constexpr int NR = k3NR, SW = kTX + 8, SP = (TY + 8) * SW;
+    static_assert(SP % 32 == 0, "ring slots must stay 128-byte aligned");
+    extern __shared__ unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar[NR];
+    float* ring = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+    const int ntz = (a.Nz + TZC - 1) / TZC;
+    const int shot = blockIdx.z / ntz, tzi = blockIdx.z - shot * ntz;
+    const int z0 = tzi * TZC, z1 = min(z0 + TZC, a.Nz);
+    const int nplanes = z1 - z0 + 8;  // planes z0-4 .. z1+3, index j = z - (z0 - 4)
+    const int lx = 4 * tx, gx = x0 + lx, gy = y0 + ty;
+    const int nvalid = min(4, a.Nx - gx);
+    const bool live = gy < a.Ny && nvalid > 0;
+    const bool pad = gy < a.Ny && nvalid <= 0 && gx < a.P;
+    const size_t so = (size_t)shot * a.cell;
+    const size_t plane = (size_t)a.Ny * a.P;
+    const size_t roff = (size_t)gy * a.P + gx;
+    const bool imaging = ADJ && a.gacc != nullptr;
+    constexpr uint32_t kBytes = SP * 4u;
+
+    auto issue = [&](int j) {
+        const int sl = j % NR;
+        mbar_expect_tx(&bar[sl], kBytes);
+        tma_load_5d(ring + sl * SP, &mp.halo3, &bar[sl], x0 - 4, y0 - 4, z0 - 4 + j, shot, a.u_buf);
+    };
+    auto waitp = [&](int j) { return mbar_wait(&bar[j % NR], (uint32_t)(j / NR) & 1u); };
+    auto own = [&](int j) { return lds4(ring + (j % NR) * SP + (ty + 4) * SW + lx + 4); };
+    int issued = -1;  // highest plane index issued (thread 0)
+    auto drain = [&](int from) {
+        // copies issued by this CTA may still land in its shared memory
+        if (tid == 0) {
+            atomicOr(a.err, kErrTimeout);
+            for (int j = from; j <= issued; ++j) waitp(j);
+        }
+    };
+
+    if (tid == 0) {
+        for (int k = 0; k < NR; ++k) mbar_init(&bar[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = 0; j < min(NR, nplanes); ++j) issue(j);
+        issued = min(NR, nplanes) - 1;
+    }
+
+    int dxy[4];
+    {
+        const int dy = sponge_depth(gy, a.nb, a.ny);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dxy[e] = max(sponge_depth(gx + e, a.nb, a.nx), dy);
+    }
+    float4 q[9];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        ok = waitp(j) && ok;
+        q[j] = own(j);
+    }
+    if (__syncthreads_or(!ok)) {
+        drain(0);
+        return;
+    }
+    if (tid == 0) {
+        for (int j = NR; j < min(NR + 4, nplanes); ++j) issue(j);
+        issued = max(issued, min(NR + 4, nplanes) - 1);
+    }
+#pragma unroll
+    for (int j = 4; j < 8; ++j) {
+        ok = waitp(j) && ok;
+        q[j] = own(j);
+    }
+
+    for (int i = 0; i < z1 - z0; ++i) {
+        const int gz = z0 + i;
+        const size_t off = gz * plane + roff;
+        float4 kp = make_float4(0.f, 0.f, 0.f, 0.f), uo = kp;
+        if (live) {
+            kp = ld4(a.kap + off);
+            uo = *reinterpret_cast<const float4*>(a.uprev + so + off);
+        }
+        ok = waitp(i + 8) && ok;
+        q[8] = own(i + 8);
+        const float* cs = ring + ((i + 4) % NR) * SP + (ty + 4) * SW + lx;  // centre plane, this thread's row
+        float* un = a.unew + so + off;
+        if (live) {
+            const float4 A = lds4(cs), B = lds4(cs + 4), C = lds4(cs + 8);
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+            float lap[4];
+            lap4_3d(w, [&](int k, float4& Up, float4& Dn, float4& Zu, float4& Zd) {
+                Up = lds4(cs + 4 - k * SW);
+                Dn = lds4(cs + 4 + k * SW);
+                Zu = q[4 - k];
+                Zd = q[4 + k];
+            }, lap);
+            const int dz = sponge_depth(gz, a.nb, a.nz);
+            const float cen[4] = {B.x, B.y, B.z, B.w};
+            const float um[4] = {uo.x, uo.y, uo.z, uo.w};
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int dd = max(dxy[e], dz);
+                const float kap = f4(kp, e);
+                const float eps = kap * a.ceps * (float)(dd * dd);
+                out[e] = leap1(cen[e], um[e], lap[e], kap, eps, __frcp_rn(1.0f + eps), 0.0f);
+            }
+            float uf[4] = {0.f, 0.f, 0.f, 0.f};
+            float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (imaging) {
+                if (a.uf16) {
+                    unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off), uf);
+                } else {
+                    const float4 v = ld4(a.uf32 + so + off);
+                    uf[0] = v.x;
+                    uf[1] = v.y;
+                    uf[2] = v.z;
+                    uf[3] = v.w;
+                }
+                gv = *reinterpret_cast<const float4*>(a.gacc + so + off);
+            }
+            write4<ADJ>(a, so, off, nvalid, out, cen, um, imaging, uf, gv);
+        } else if (pad) {
+            *reinterpret_cast<float4*>(un) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+        // every thread is done with the centre slot of this plane: refill it
+        if (__syncthreads_or(!ok)) {
+            drain(i + 8);
+            return;
+        }
+        if (tid == 0 && i + 4 + NR < nplanes) {
+            fence_proxy_async();
+            issue(i + 4 + NR);
+            issued = i + 4 + NR;
+        }
+    }
+    if (a.inj.cell_start || a.gat.cell_start) {
+        // the tile covers TY / TY_cell tap cells in y and TZC / TZc in z
+        const int kcell = TZC / a.TZc;
+        const int c0 = tzi * kcell, c1 = min(c0 + kcell, a.ncz);
+        for (int cy = blockIdx.y * (TY / 8); cy < min((int)(blockIdx.y + 1) * (TY / 8), a.ncy); ++cy) {
+            const int cbase = ((shot * a.ncx + (int)blockIdx.x) * a.ncy + cy) * a.ncz;
+            int ib = 0, ie = 0, gb = 0, ge = 0;
+            if (a.inj.cell_start) {
+                ib = a.inj.cell_start[cbase + c0];
+                ie = a.inj.cell_start[cbase + c1];
+            }
+            if (a.gat.cell_start) {
+                gb = a.gat.cell_start[cbase + c0];
+                ge = a.gat.cell_start[cbase + c1];
+            }
+            sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * TY);
+            __syncthreads();
+        }
     }
 }
 
@@ -1397,34 +1576,58 @@ static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2
                                    {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
                                    {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}, {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0},
                                    {5, 32, 8, 0, 0}};
-static int g_selected[2] = {-1, -1};
-static const int kDefault2D[2] = {9, 7};
+// 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y): kind 0 is
+// the z-march with a shared-memory halo plane, kind 6 the TMA plane ring.
+static const Variant2D k3D[] = {{0, 32, 8, 0, 0}, {6, 32, 8, 7, 0}, {6, 64, 8, 7, 0}, {6, 32, 16, 7, 0},
+                                {6, 64, 16, 7, 0}};
+static int g_selected[3] = {-1, -1, -1};
+static const int kDefaultVariant[3] = {18, 16, 2};
 
 int variant_count(int which)
 {
-    return which == 0 ? (int)(sizeof(kFwd2D) / sizeof(kFwd2D[0]))
-                      : (which == 1 ? (int)(sizeof(kAdj2D) / sizeof(kAdj2D[0])) : 0);
+    switch (which) {
+    case 0: return (int)(sizeof(kFwd2D) / sizeof(kFwd2D[0]));
+    case 1: return (int)(sizeof(kAdj2D) / sizeof(kAdj2D[0]));
+    case 2: return (int)(sizeof(k3D) / sizeof(k3D[0]));
+    default: return 0;
+    }
 }
 
 Variant2D variant_info(int which, int v)
 {
     if (v < 0 || v >= variant_count(which)) return Variant2D{-1, 0, 0, 0, 0};
-    return which == 0 ? kFwd2D[v] : kAdj2D[v];
+    return which == 0 ? kFwd2D[v] : (which == 1 ? kAdj2D[v] : k3D[v]);
 }
 
 int current_variant(int which)
 {
-    if (which < 0 || which > 1) return -1;
-    return g_selected[which] >= 0 ? g_selected[which] : kDefault2D[which];
+    if (which < 0 || which > 2) return -1;
+    return g_selected[which] >= 0 ? g_selected[which] : kDefaultVariant[which];
 }
 
-bool variant_forced(int which) { return which >= 0 && which <= 1 && g_selected[which] >= 0; }
+bool variant_forced(int which) { return which >= 0 && which <= 2 && g_selected[which] >= 0; }
 
 int select_variant(int which, int v)
 {
-    if (which < 0 || which > 1 || v < -1 || v >= variant_count(which)) return -1;
+    if (which < 0 || which > 2 || v < -1 || v >= variant_count(which)) return -1;
     g_selected[which] = v;
     return 0;
+}
+
+template <int TY, int TZC>
+static void launch_3d_tma(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+{
+    constexpr size_t smem = (size_t)k3NR * (TY + 8) * (kTX + 8) * 4 + 128;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    const int ntz = (a.Nz + TZC - 1) / TZC;
+    dim3 grid(a.ncx, (a.Ny + TY - 1) / TY, ntz * a.nshot);
+    if (adjoint) k_step3d_tma<TY, TZC, true><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+    else k_step3d_tma<TY, TZC, false><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
 }
 
 template <int TZ, int BZ, int G, bool ADJ>
@@ -1583,11 +1786,19 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             }
         }
     } else {
-        const int ntz = (a.Nz + 31) / 32;
-        dim3 grid(t.ncx, t.ncy, ntz * a.nshot);
-        dim3 block(32, 8);
-        if (adjoint) k_step3d<8, 32, true><<<grid, block, 0, s>>>(a);
-        else k_step3d<8, 32, false><<<grid, block, 0, s>>>(a);
+        switch (a.dmv ? 0 : t.v3) {  // the Born source is carried by the z-march kernel only
+        case 1: launch_3d_tma<8, 32>(adjoint, a, maps, s); break;
+        case 2: launch_3d_tma<8, 64>(adjoint, a, maps, s); break;
+        case 3: launch_3d_tma<16, 32>(adjoint, a, maps, s); break;
+        case 4: launch_3d_tma<16, 64>(adjoint, a, maps, s); break;
+        default: {
+            const int ntz = (a.Nz + 31) / 32;
+            dim3 grid(t.ncx, t.ncy, ntz * a.nshot);
+            dim3 block(32, 8);
+            if (adjoint) k_step3d<8, 32, true><<<grid, block, 0, s>>>(a);
+            else k_step3d<8, 32, false><<<grid, block, 0, s>>>(a);
+        }
+        }
     }
 }
 

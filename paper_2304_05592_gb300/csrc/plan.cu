@@ -48,7 +48,7 @@ Tiling choose_tiling(const Dims& d, int nshot)
 {
     Tiling t;
     t.TX = kTX;
-    t.vf = t.va = -1;
+    t.vf = t.va = t.v3 = -1;
     if (d.ndim == 2) {
         t.TY = 1;
         t.TZc = kTZc2;
@@ -64,6 +64,7 @@ Tiling choose_tiling(const Dims& d, int nshot)
     } else {
         t.TY = 8;
         t.TZc = 32;
+        t.v3 = current_variant(2);
     }
     t.ncx = (d.Nx + t.TX - 1) / t.TX;
     t.ncy = (d.Ny + t.TY - 1) / t.TY;

@@ -35,6 +35,32 @@ __device__ __forceinline__ void lap4(const float* w, ZN zn, float* lap)
     }
 }
 
+// 3D Laplacian of 4 consecutive x points: w as in lap4; zn(k, Up, Dn, Zu, Zd)
+// returns the 4 points' values k rows away in y (Up, Dn) and k planes away in
+// z (Zu, Zd).  Order: 3 c0 w, + c_k (w_{-k} + w_{+k}) along x, then
+// + c_k ((Up + Dn) + (Zu + Zd)) for k = 1..4.
+template <class ZN>
+__device__ __forceinline__ void lap4_3d(const float* w, ZN zn, float* lap)
+{
+    const float ck[5] = {kC0, kC1, kC2, kC3, kC4};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float acc = (3.0f * kC0) * w[e + 4];
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) acc = fmaf(ck[k], w[e + 4 - k] + w[e + 4 + k], acc);
+        lap[e] = acc;
+    }
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        float4 Up, Dn, Zu, Zd;
+        zn(k, Up, Dn, Zu, Zd);
+        lap[0] = fmaf(ck[k], (Up.x + Dn.x) + (Zu.x + Zd.x), lap[0]);
+        lap[1] = fmaf(ck[k], (Up.y + Dn.y) + (Zu.y + Zd.y), lap[1]);
+        lap[2] = fmaf(ck[k], (Up.z + Dn.z) + (Zu.z + Zd.z), lap[2]);
+        lap[3] = fmaf(ck[k], (Up.w + Dn.w) + (Zu.w + Zd.w), lap[3]);
+    }
+}
+
 // Leapfrog update of one point: (kap lap + eps um + 2 c - um - src) * inv,
 // inv = 1 / (1 + eps); src is the Born secondary source (zero elsewhere).
 __device__ __forceinline__ float leap1(float c, float um, float lap, float kap, float eps, float inv, float src)
