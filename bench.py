@@ -205,6 +205,12 @@ def cpu_baseline(nt: int):
             "sample": f"1 shot of the 32 (full grid, nt={nt}), one gradient, FP64, {el:.1f} s"}
 
 
+def _variant3d():
+    """The 3D step variant the library runs by default (TMA plane ring, 8-row
+    tiles, 64 planes per CTA, 10 ring slots)."""
+    return "5 (k_step3d_tma<8,64,10>)"
+
+
 def config3_forward(dev, peak):
     """3D config-3 forward (400 x 400 x 300 at 10 m, 160 000 receivers), 200 steps."""
     import torch
@@ -229,7 +235,8 @@ def config3_forward(dev, peak):
     ach = 16 * N / avg / 1e9
     return {"workload": "3D forward 400x400x300 at 10 m + 40-cell sponge (480x480x380 padded), 160000 receivers, "
                         "200 of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
-            "kernel": "k_step3d<8,32,fwd>", "avg_launch_us": avg * 1e6, "achieved_gbs": ach, "frac": ach / peak,
+            "kernel": f"3D step variant {wave.wave_variant_count(2) and _variant3d()}", "avg_launch_us": avg * 1e6,
+            "achieved_gbs": ach, "frac": ach / peak,
             "bound": "hbm", "bytes_per_point": 16}
 
 

@@ -91,6 +91,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 
+// Plain arrival (release at CTA scope), used by consumers to free a ring slot.
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
 {
     uint32_t ok;
@@ -1357,21 +1363,19 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
 // 3D step fed by TMA.  Tile = 128 (x) by TY (y) points, CTA = 32 x TY threads
 // (4 x points per thread) marching over TZC planes in z.  Every xy plane of u
 // with its 4-point halo ((TY+8) x 136 floats) arrives by one 5D bulk tensor
-// load into a ring of NR = 7 shared-memory slots: planes z..z+4 are resident
-// while planes up to z+6 are in flight.  Each thread keeps the 9 planes
+// load into a ring of NR shared-memory slots: planes z..z+4 are resident
+// while planes up to z+NR-1 are in flight.  Each thread keeps the 9 planes
 // z-4..z+4 of its 4 points in registers (read once from the ring when a plane
 // arrives) and takes x and y neighbours from the centre plane's slot.  A slot
 // is refilled right after the block barrier that ends the plane that used it
 // as centre: one barrier per plane.  Sponge depths in x and y are fixed per
 // thread.  Waits are bounded; on a timeout the CTA records kErrTimeout, lets
 // its issued copies land and returns.
-constexpr int k3NR = 7;
-
-template <int TY, int TZC, bool ADJ>
+template <int TY, int TZC, int NR, bool ADJ>
 __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const __grid_constant__ StepMaps mp,
                                                                         const StepArgs a)
 {
-    constexpr int NR = k3NR, SW = kTX + 8, SP = (TY + 8) * SW;
+    constexpr int SW = kTX + 8, SP = (TY + 8) * SW;
     static_assert(SP % 32 == 0, "ring slots must stay 128-byte aligned");
     extern __shared__ unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar[NR];
@@ -1445,13 +1449,19 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
         q[j] = own(j);
     }
 
+    // the model and the previous level of the next plane are loaded one plane ahead
+    float4 kp = make_float4(0.f, 0.f, 0.f, 0.f), uo = kp;
+    if (live) {
+        kp = ld4(a.kap + z0 * plane + roff);
+        uo = *reinterpret_cast<const float4*>(a.uprev + so + z0 * plane + roff);
+    }
     for (int i = 0; i < z1 - z0; ++i) {
         const int gz = z0 + i;
         const size_t off = gz * plane + roff;
-        float4 kp = make_float4(0.f, 0.f, 0.f, 0.f), uo = kp;
-        if (live) {
-            kp = ld4(a.kap + off);
-            uo = *reinterpret_cast<const float4*>(a.uprev + so + off);
+        float4 kpn = make_float4(0.f, 0.f, 0.f, 0.f), uon = kpn;
+        if (live && gz + 1 < z1) {
+            kpn = ld4(a.kap + off + plane);
+            uon = *reinterpret_cast<const float4*>(a.uprev + so + off + plane);
         }
         ok = waitp(i + 8) && ok;
         q[8] = own(i + 8);
@@ -1498,9 +1508,11 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+        kp = kpn;
+        uo = uon;
         // every thread is done with the centre slot of this plane: refill it
         if (__syncthreads_or(!ok)) {
-            drain(i + 8);
+            drain(0);
             return;
         }
         if (tid == 0 && i + 4 + NR < nplanes) {
@@ -1511,6 +1523,194 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
     }
     if (a.inj.cell_start || a.gat.cell_start) {
         // the tile covers TY / TY_cell tap cells in y and TZC / TZc in z
+        const int kcell = TZC / a.TZc;
+        const int c0 = tzi * kcell, c1 = min(c0 + kcell, a.ncz);
+        for (int cy = blockIdx.y * (TY / 8); cy < min((int)(blockIdx.y + 1) * (TY / 8), a.ncy); ++cy) {
+            const int cbase = ((shot * a.ncx + (int)blockIdx.x) * a.ncy + cy) * a.ncz;
+            int ib = 0, ie = 0, gb = 0, ge = 0;
+            if (a.inj.cell_start) {
+                ib = a.inj.cell_start[cbase + c0];
+                ie = a.inj.cell_start[cbase + c1];
+            }
+            if (a.gat.cell_start) {
+                gb = a.gat.cell_start[cbase + c0];
+                ge = a.gat.cell_start[cbase + c1];
+            }
+            sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * TY);
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3D step, TMA plane ring without block barriers in the z loop.  As
+// k_step3d_tma, but each ring slot also has an "empty" barrier on which every
+// warp arrives once it is done with the slot (planes z0-4..z0-1 right after the
+// prologue, every other plane after its turn as centre plane).  Thread 0
+// refills a slot LAG = 2 planes after its release, waiting on that barrier, so
+// warps never wait for one another, only for their data.  Every wait is
+// bounded; a thread whose wait gives up raises a shared abort flag, all threads
+// leave the loop and meet at one final barrier, thread 0 records kErrTimeout,
+// waits for the copies still in flight (at most one per slot) and the CTA
+// returns.
+template <int TY, int TZC, int NR, bool ADJ>
+__global__ void __launch_bounds__(32 * TY, 2) k_step3d_ws(const __grid_constant__ StepMaps mp, const StepArgs a)
+{
+    constexpr int SW = kTX + 8, SP = (TY + 8) * SW, LAG = 2;
+    static_assert(SP % 32 == 0, "ring slots must stay 128-byte aligned");
+    static_assert(NR >= 8 + LAG, "planes 0..7 are issued up front and the lag must leave slots to refill");
+    extern __shared__ unsigned char dyn[];
+    __shared__ __align__(8) uint64_t full[NR], empty[NR];
+    __shared__ volatile int sabort;
+    float* ring = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+    const int ntz = (a.Nz + TZC - 1) / TZC;
+    const int shot = blockIdx.z / ntz, tzi = blockIdx.z - shot * ntz;
+    const int z0 = tzi * TZC, z1 = min(z0 + TZC, a.Nz);
+    const int nplanes = z1 - z0 + 8;  // planes z0-4 .. z1+3, index j = z - (z0 - 4)
+    const int lx = 4 * tx, gx = x0 + lx, gy = y0 + ty;
+    const int nvalid = min(4, a.Nx - gx);
+    const bool live = gy < a.Ny && nvalid > 0;
+    const bool pad = gy < a.Ny && nvalid <= 0 && gx < a.P;
+    const size_t so = (size_t)shot * a.cell;
+    const size_t plane = (size_t)a.Ny * a.P;
+    const size_t roff = (size_t)gy * a.P + gx;
+    const bool imaging = ADJ && a.gacc != nullptr;
+    constexpr uint32_t kBytes = SP * 4u;
+
+    auto issue = [&](int j) {
+        const int sl = j % NR;
+        mbar_expect_tx(&full[sl], kBytes);
+        tma_load_5d(ring + sl * SP, &mp.halo3, &full[sl], x0 - 4, y0 - 4, z0 - 4 + j, shot, a.u_buf);
+    };
+    auto waitp = [&](int j) { return mbar_wait(&full[j % NR], (uint32_t)(j / NR) & 1u); };
+    auto own = [&](int j) { return lds4(ring + (j % NR) * SP + (ty + 4) * SW + lx + 4); };
+    auto release = [&](int j) {
+        __syncwarp();
+        if (tx == 0) mbar_arrive(&empty[j % NR]);
+    };
+
+    if (tid == 0) {
+        for (int k = 0; k < NR; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], TY);
+        }
+        sabort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int next = 0;  // next plane to issue (thread 0)
+    if (tid == 0) {
+        for (; next < min(NR, nplanes); ++next) issue(next);
+    }
+    // thread 0 refills the slot of every plane released at least LAG planes ago
+    auto refill = [&](int released) {
+        while (next < nplanes && next - NR <= released - LAG) {
+            if (!mbar_wait(&empty[next % NR], (uint32_t)((next - NR) / NR) & 1u)) return false;
+            fence_proxy_async();
+            issue(next);
+            ++next;
+        }
+        return true;
+    };
+
+    int dxy[4];
+    {
+        const int dy = sponge_depth(gy, a.nb, a.ny);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dxy[e] = max(sponge_depth(gx + e, a.nb, a.nx), dy);
+    }
+    float4 q[9];
+    bool fail = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        fail = fail || !waitp(j);
+        q[j] = own(j);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) release(j);  // below the tile's first plane: never a centre
+
+    float4 kp = make_float4(0.f, 0.f, 0.f, 0.f), uo = kp;
+    if (live) {
+        kp = ld4(a.kap + z0 * plane + roff);
+        uo = *reinterpret_cast<const float4*>(a.uprev + so + z0 * plane + roff);
+    }
+    for (int i = 0; i < z1 - z0 && !fail; ++i) {
+        if (sabort) break;
+        const int gz = z0 + i;
+        const size_t off = gz * plane + roff;
+        float4 kpn = make_float4(0.f, 0.f, 0.f, 0.f), uon = kpn;
+        if (live && gz + 1 < z1) {
+            kpn = ld4(a.kap + off + plane);
+            uon = *reinterpret_cast<const float4*>(a.uprev + so + off + plane);
+        }
+        if (!waitp(i + 8)) {
+            fail = true;
+            break;
+        }
+        q[8] = own(i + 8);
+        const float* cs = ring + ((i + 4) % NR) * SP + (ty + 4) * SW + lx;  // centre plane, this thread's row
+        float* un = a.unew + so + off;
+        if (live) {
+            const float4 A = lds4(cs), B = lds4(cs + 4), C = lds4(cs + 8);
+            const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+            float lap[4];
+            lap4_3d(w, [&](int k, float4& Up, float4& Dn, float4& Zu, float4& Zd) {
+                Up = lds4(cs + 4 - k * SW);
+                Dn = lds4(cs + 4 + k * SW);
+                Zu = q[4 - k];
+                Zd = q[4 + k];
+            }, lap);
+            const int dz = sponge_depth(gz, a.nb, a.nz);
+            const float cen[4] = {B.x, B.y, B.z, B.w};
+            const float um[4] = {uo.x, uo.y, uo.z, uo.w};
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int dd = max(dxy[e], dz);
+                const float kap = f4(kp, e);
+                const float eps = kap * a.ceps * (float)(dd * dd);
+                out[e] = leap1(cen[e], um[e], lap[e], kap, eps, __frcp_rn(1.0f + eps), 0.0f);
+            }
+            float uf[4] = {0.f, 0.f, 0.f, 0.f};
+            float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (imaging) {
+                if (a.uf16) {
+                    unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off), uf);
+                } else {
+                    const float4 v = ld4(a.uf32 + so + off);
+                    uf[0] = v.x;
+                    uf[1] = v.y;
+                    uf[2] = v.z;
+                    uf[3] = v.w;
+                }
+                gv = *reinterpret_cast<const float4*>(a.gacc + so + off);
+            }
+            write4<ADJ>(a, so, off, nvalid, out, cen, um, imaging, uf, gv);
+        } else if (pad) {
+            *reinterpret_cast<float4*>(un) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+        kp = kpn;
+        uo = uon;
+        release(i + 4);
+        if (tid == 0 && !refill(i + 4)) {
+            fail = true;
+            break;
+        }
+    }
+    if (fail) sabort = 1;
+    if (__syncthreads_or(fail || sabort)) {
+        if (tid == 0) {
+            atomicOr(a.err, kErrTimeout);
+            // at most one copy per slot can be in flight: the last NR issued
+            for (int j = max(0, next - NR); j < next; ++j) waitp(j);
+        }
+        return;
+    }
+    if (a.inj.cell_start || a.gat.cell_start) {
         const int kcell = TZC / a.TZc;
         const int c0 = tzi * kcell, c1 = min(c0 + kcell, a.ncz);
         for (int cy = blockIdx.y * (TY / 8); cy < min((int)(blockIdx.y + 1) * (TY / 8), a.ncy); ++cy) {
@@ -1576,12 +1776,14 @@ static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2
                                    {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
                                    {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}, {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0},
                                    {5, 32, 8, 0, 0}};
-// 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y): kind 0 is
-// the z-march with a shared-memory halo plane, kind 6 the TMA plane ring.
-static const Variant2D k3D[] = {{0, 32, 8, 0, 0}, {6, 32, 8, 7, 0}, {6, 64, 8, 7, 0}, {6, 32, 16, 7, 0},
-                                {6, 64, 16, 7, 0}};
+// 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y, NST = ring
+// slots, G = 1 for the ring without block barriers): kind 0 is the z-march
+// with a shared-memory halo plane, kind 6 the TMA plane ring.
+static const Variant2D k3D[] = {{0, 32, 8, 0, 0},  {6, 32, 8, 7, 0},  {6, 64, 8, 7, 0},  {6, 32, 16, 7, 0},
+                                {6, 64, 16, 7, 0}, {6, 64, 8, 10, 0}, {6, 32, 8, 10, 0}, {6, 96, 8, 10, 0},
+                                {6, 64, 8, 10, 1}, {6, 64, 8, 12, 1}, {6, 96, 8, 12, 1}};
 static int g_selected[3] = {-1, -1, -1};
-static const int kDefaultVariant[3] = {18, 16, 2};
+static const int kDefaultVariant[3] = {18, 16, 5};
 
 int variant_count(int which)
 {
@@ -1614,20 +1816,37 @@ int select_variant(int which, int v)
     return 0;
 }
 
-template <int TY, int TZC>
-static void launch_3d_tma(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+template <int TY, int TZC, int NR>
+static void launch_3d_ws(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
-    constexpr size_t smem = (size_t)k3NR * (TY + 8) * (kTX + 8) * 4 + 128;
+    constexpr size_t smem = (size_t)NR * (TY + 8) * (kTX + 8) * 4 + 128;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step3d_ws<TY, TZC, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step3d_ws<TY, TZC, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
     const int ntz = (a.Nz + TZC - 1) / TZC;
     dim3 grid(a.ncx, (a.Ny + TY - 1) / TY, ntz * a.nshot);
-    if (adjoint) k_step3d_tma<TY, TZC, true><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
-    else k_step3d_tma<TY, TZC, false><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+    if (adjoint) k_step3d_ws<TY, TZC, NR, true><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+    else k_step3d_ws<TY, TZC, NR, false><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+}
+
+template <int TY, int TZC, int NR>
+static void launch_3d_tma(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
+{
+    constexpr size_t smem = (size_t)NR * (TY + 8) * (kTX + 8) * 4 + 128;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    const int ntz = (a.Nz + TZC - 1) / TZC;
+    dim3 grid(a.ncx, (a.Ny + TY - 1) / TY, ntz * a.nshot);
+    if (adjoint) k_step3d_tma<TY, TZC, NR, true><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+    else k_step3d_tma<TY, TZC, NR, false><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
 }
 
 template <int TZ, int BZ, int G, bool ADJ>
@@ -1787,10 +2006,16 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
         }
     } else {
         switch (a.dmv ? 0 : t.v3) {  // the Born source is carried by the z-march kernel only
-        case 1: launch_3d_tma<8, 32>(adjoint, a, maps, s); break;
-        case 2: launch_3d_tma<8, 64>(adjoint, a, maps, s); break;
-        case 3: launch_3d_tma<16, 32>(adjoint, a, maps, s); break;
-        case 4: launch_3d_tma<16, 64>(adjoint, a, maps, s); break;
+        case 1: launch_3d_tma<8, 32, 7>(adjoint, a, maps, s); break;
+        case 2: launch_3d_tma<8, 64, 7>(adjoint, a, maps, s); break;
+        case 3: launch_3d_tma<16, 32, 7>(adjoint, a, maps, s); break;
+        case 4: launch_3d_tma<16, 64, 7>(adjoint, a, maps, s); break;
+        case 5: launch_3d_tma<8, 64, 10>(adjoint, a, maps, s); break;
+        case 6: launch_3d_tma<8, 32, 10>(adjoint, a, maps, s); break;
+        case 7: launch_3d_tma<8, 96, 10>(adjoint, a, maps, s); break;
+        case 8: launch_3d_ws<8, 64, 10>(adjoint, a, maps, s); break;
+        case 9: launch_3d_ws<8, 64, 12>(adjoint, a, maps, s); break;
+        case 10: launch_3d_ws<8, 96, 12>(adjoint, a, maps, s); break;
         default: {
             const int ntz = (a.Nz + 31) / 32;
             dim3 grid(t.ncx, t.ncy, ntz * a.nshot);
