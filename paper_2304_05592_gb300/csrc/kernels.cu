@@ -545,19 +545,21 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
 // stencil arithmetic, one load of the previous level and one store per 4
 // points.  Waits on the ring are bounded; on a timeout the CTA records
 // kErrTimeout, lets its issued copies land and returns.
-template <int TZ, int BZ, int G, bool ADJ>
+template <int TZ, int BZ, int G, bool PT, bool ADJ>
 __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ))
     k_step2d_sgt(const __grid_constant__ StepMaps mp, const StepArgs a)
 {
     constexpr int SW = kTX + 8;
     constexpr int RB = TZ / BZ;
-    constexpr int SU = (TZ + 8) * SW;  // floats in one stage
-    static_assert(SU % 32 == 0, "stages must stay 128-byte aligned");
+    constexpr int SU = (TZ + 8) * SW;          // halo tile of u
+    constexpr int SU2 = SU + (PT ? TZ * kTX : 0);  // one stage (+ the previous level's tile with PT)
+    static_assert(SU % 32 == 0 && SU2 % 32 == 0, "stages must stay 128-byte aligned");
     extern __shared__ unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar[2];
     float* st = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
-    float* sg = st + 2 * SU;  // [TZ][kTX] gradient tile (adjoint with imaging)
+    float* sg = st + 2 * SU2;  // [TZ][kTX] gradient tile (adjoint with imaging)
     const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
+    const CUtensorMap* mt = ADJ ? &mp.tile_a : &mp.tile_f;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int x0 = blockIdx.x * kTX, z0 = blockIdx.y * TZ;
     const int grp = blockIdx.z, s0 = grp * G, ns = min(G, a.nshot - s0);
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
     const int nvalid = min(4, a.Nx - gx);
     const bool imaging = ADJ && a.gacc != nullptr;
     const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
-    constexpr uint32_t kBytes = SU * 4u;
+    constexpr uint32_t kBytes = SU2 * 4u;
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -576,6 +578,7 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
     if (tid == 0) {
         mbar_expect_tx(&bar[0], kBytes);
         tma_load_4d(st, mh, &bar[0], x0 - 4, z0 - 4, s0, a.u_buf);
+        if (PT) tma_load_4d(st + SU, mt, &bar[0], x0, z0, s0, a.prev_buf);
     }
 
     int off[RB];
@@ -613,14 +616,17 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
         if (tid == 0 && i + 1 < ns) {
             fence_proxy_async();
             mbar_expect_tx(&bar[stage ^ 1], kBytes);
-            tma_load_4d(st + (stage ^ 1) * SU, mh, &bar[stage ^ 1], x0 - 4, z0 - 4, shot + 1, a.u_buf);
+            tma_load_4d(st + (stage ^ 1) * SU2, mh, &bar[stage ^ 1], x0 - 4, z0 - 4, shot + 1, a.u_buf);
+            if (PT) tma_load_4d(st + (stage ^ 1) * SU2 + SU, mt, &bar[stage ^ 1], x0, z0, shot + 1, a.prev_buf);
         }
         const size_t so = (size_t)shot * a.cell;
         float4 uo[RB];
+        if (!PT) {
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr)
-            uo[rr] = live[rr] ? *reinterpret_cast<const float4*>(a.uprev + so + off[rr])
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int rr = 0; rr < RB; ++rr)
+                uo[rr] = live[rr] ? *reinterpret_cast<const float4*>(a.uprev + so + off[rr])
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const bool ok = mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -631,7 +637,11 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
             }
             return;
         }
-        const float* sb = st + stage * SU;
+        const float* sb = st + stage * SU2;
+        if (PT) {
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) uo[rr] = lds4(sb + SU + (ty + rr * BZ) * kTX + lx);
+        }
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr) {
             const int r = ty + rr * BZ;
@@ -1768,14 +1778,15 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0}, {1, 32, 1, 3, 0}, {2, 16, 8, 0, 8},
                                    {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}, {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4},
                                    {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2}, {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4},
-                                   {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0}, {5, 32, 8, 0, 0}};
+                                   {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0}, {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2},
+                                   {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
                                    {1, 16, 1, 4, 0}, {2, 16, 8, 0, 8}, {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8},
                                    {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
                                    {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}, {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0},
-                                   {5, 32, 8, 0, 0}};
+                                   {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2}, {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}};
 // 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y, NST = ring
 // slots, G = 1 for the ring without block barriers): kind 0 is the z-march
 // with a shared-memory halo plane, kind 6 the TMA plane ring.
@@ -1862,17 +1873,17 @@ static void launch_2d_group(const StepArgs& a, cudaStream_t s)
     k_step2d_sg<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(a);
 }
 
-template <int TZ, int BZ, int G, bool ADJ>
+template <int TZ, int BZ, int G, bool ADJ, bool PT = false>
 static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
-    constexpr size_t smem = (size_t)(2 * (TZ + 8) * (kTX + 8) + (ADJ ? TZ * kTX : 0)) * 4 + 128;
+    constexpr size_t smem = (size_t)(2 * ((TZ + 8) * (kTX + 8) + (PT ? TZ * kTX : 0)) + (ADJ ? TZ * kTX : 0)) * 4 + 128;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, PT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
     dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
-    k_step2d_sgt<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
+    k_step2d_sgt<TZ, BZ, G, PT, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
 }
 
 template <int TZ, int BZ, bool ADJ>
@@ -1973,6 +1984,9 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 24: launch_2d_persistent<16, 8, false>(a, maps, s); break;
             case 25: launch_2d_persistent<8, 8, false>(a, maps, s); break;
             case 26: launch_2d_persistent<32, 8, false>(a, maps, s); break;
+            case 27: launch_2d_group_tma<16, 8, 2, false, true>(a, maps, s); break;
+            case 28: launch_2d_group_tma<16, 8, 4, false, true>(a, maps, s); break;
+            case 29: launch_2d_group_tma<8, 8, 4, false, true>(a, maps, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -2001,6 +2015,9 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 22: launch_2d_persistent<16, 8, true>(a, maps, s); break;
             case 23: launch_2d_persistent<8, 8, true>(a, maps, s); break;
             case 24: launch_2d_persistent<32, 8, true>(a, maps, s); break;
+            case 25: launch_2d_group_tma<16, 8, 2, true, true>(a, maps, s); break;
+            case 26: launch_2d_group_tma<16, 8, 4, true, true>(a, maps, s); break;
+            case 27: launch_2d_group_tma<8, 8, 4, true, true>(a, maps, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }
