@@ -192,6 +192,37 @@ typedef struct {
     double misfit;         /* out: 1/2 ||F q - d_obs||^2 of this problem    */
 } wave_problem_t;
 
+/* Low-cut wavelet for the paper's FWI experiment ("Ricker wavelet with no
+ * energy below 4Hz", section "Deep priors and normalizing flows"): the real
+ * DFT of q (nt samples, spacing dt) is multiplied by H(f) = 0 below f_cut, the
+ * raised-cosine ramp 0.5 (1 - cos(pi (f - f_cut) / (f_pass - f_cut))) up to
+ * f_pass and 1 above (f_k = k / (nt dt), k = 0..nt/2), and transformed back.
+ * The DFT and its inverse are direct sums in double.  q and out are device
+ * arrays of nt floats (out may not alias q); work holds
+ * wave_lowcut_work_bytes(nt) device bytes.  Stream-ordered, no
+ * synchronisation; WAVE_ERR_ARG for null pointers, nt < 1, dt <= 0 or
+ * f_pass <= f_cut. */
+size_t wave_lowcut_work_bytes(int nt);
+wave_status_t wave_lowcut(const float* q, int nt, float dt, float f_cut, float f_pass, float* out, void* work,
+                          void* stream);
+
+/* Additive coloured Gaussian noise with the bandwidth of the data (the same
+ * experiment): noise[s][t][r] = sum_k filt[k] white[s][t - k + center][r]
+ * (zero outside the trace), scaled so that 20 log10(||data|| / ||noise||) =
+ * snr_db, and out = data + noise.  data, white and out are device arrays
+ * [nshot][nt][nrec] (white holds the caller's standard normal draws; out may
+ * alias data); filt is a device array of nf taps, normally the source
+ * wavelet, so that the noise has the data's band.  work holds
+ * wave_add_noise_work_bytes(nshot, nt, nrec) device bytes.  Stream-ordered. */
+size_t wave_add_noise_work_bytes(int nshot, int nt, int nrec);
+wave_status_t wave_add_noise(const float* data, const float* white, int nshot, int nt, int nrec, const float* filt,
+                             int nf, int center, double snr_db, float* out, void* work, void* stream);
+
+/* Model updates of an FWI iteration: y += alpha x, and y = min(max(y, lo), hi)
+ * (n device floats each).  Stream-ordered. */
+wave_status_t wave_axpy(long long n, float alpha, const float* x, float* y, void* stream);
+wave_status_t wave_clamp(long long n, float lo, float hi, float* y, void* stream);
+
 /* The bounded wait that the persistent batch sweep uses between tiles, run by
  * one thread on a caller-given device flag: it polls *flag >= want through L2
  * and gives up after a fixed number of polls (a few seconds) or as soon as

@@ -103,6 +103,20 @@ def _lib():
         lib.wave_workspace_size_batch.restype = I
         lib.wave_gradient_batch.argtypes = [ctypes.POINTER(wave_problem_t), I, I, I, I, P, ctypes.c_size_t, P]
         lib.wave_gradient_batch.restype = I
+        L = ctypes.c_longlong
+        F = ctypes.c_float
+        lib.wave_lowcut_work_bytes.argtypes = [I]
+        lib.wave_lowcut_work_bytes.restype = ctypes.c_size_t
+        lib.wave_lowcut.argtypes = [P, I, F, F, F, P, P, P]
+        lib.wave_lowcut.restype = I
+        lib.wave_add_noise_work_bytes.argtypes = [I, I, I]
+        lib.wave_add_noise_work_bytes.restype = ctypes.c_size_t
+        lib.wave_add_noise.argtypes = [P, P, I, I, I, P, I, I, ctypes.c_double, P, P, P]
+        lib.wave_add_noise.restype = I
+        lib.wave_axpy.argtypes = [L, F, P, P, P]
+        lib.wave_axpy.restype = I
+        lib.wave_clamp.argtypes = [L, F, F, P, P]
+        lib.wave_clamp.restype = I
         lib.wave_wait_probe.argtypes = [P, I, P, P, P]
         lib.wave_wait_probe.restype = I
         lib.wave_set_variant.argtypes = [I, I]
@@ -482,3 +496,57 @@ def wave_wait_probe(flag: torch.Tensor, want: int, abort_word: torch.Tensor, err
     return int(_lib().wave_wait_probe(ctypes.c_void_p(flag.data_ptr()), int(want),
                                       ctypes.c_void_p(abort_word.data_ptr()), ctypes.c_void_p(err.data_ptr()),
                                       _stream(stream)))
+
+
+def wave_lowcut(q: torch.Tensor, dt: float, f_cut: float = 4.0, f_pass: float = 6.0, out=None,
+                stream=None) -> torch.Tensor:
+    """q [nt] high-passed: no energy below f_cut, a raised-cosine ramp up to f_pass."""
+    nt = q.numel()
+    _dev(q, "q", (nt,))
+    if out is None:
+        out = torch.empty_like(q)
+    _dev(out, "out", (nt,))
+    work = _workspace(int(_lib().wave_lowcut_work_bytes(nt)), q.device)
+    st = _lib().wave_lowcut(q.data_ptr(), nt, float(dt), float(f_cut), float(f_pass), out.data_ptr(),
+                            work.data_ptr(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_lowcut")
+    return out
+
+
+def wave_add_noise(data: torch.Tensor, white: torch.Tensor, filt: torch.Tensor, center: int, snr_db: float,
+                   out=None, stream=None) -> torch.Tensor:
+    """data [nshot][nt][nrec] plus white noise filtered by filt (centred at tap
+    `center`), scaled to snr_db."""
+    ns, nt, nrec = data.shape
+    _dev(data, "data")
+    _dev(white, "white", data.shape)
+    _dev(filt, "filt", (filt.numel(),))
+    if out is None:
+        out = torch.empty_like(data)
+    _dev(out, "out", data.shape)
+    work = _workspace(int(_lib().wave_add_noise_work_bytes(ns, nt, nrec)), data.device)
+    st = _lib().wave_add_noise(data.data_ptr(), white.data_ptr(), ns, nt, nrec, filt.data_ptr(), filt.numel(),
+                               int(center), float(snr_db), out.data_ptr(), work.data_ptr(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_add_noise")
+    return out
+
+
+def wave_axpy(alpha: float, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y += alpha x in place."""
+    _dev(x, "x")
+    _dev(y, "y", x.shape)
+    st = _lib().wave_axpy(y.numel(), float(alpha), x.data_ptr(), y.data_ptr(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_axpy")
+    return y
+
+
+def wave_clamp(y: torch.Tensor, lo: float, hi: float, stream=None) -> torch.Tensor:
+    """y = min(max(y, lo), hi) in place."""
+    _dev(y, "y")
+    st = _lib().wave_clamp(y.numel(), float(lo), float(hi), y.data_ptr(), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_clamp")
+    return y
