@@ -39,8 +39,9 @@ FALLBACK_HBM_GBS = 6800.0
 # time; a kernel whose source has changed since gets null.
 VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,fwd>"),
                   (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,adj>")}
-TRAFFIC = {("k_step2d_sgt<16,8,2,fwd>", "ceb353c43c594793"): 82.16e6,
-           ("k_step2d_sgt<16,8,2,adj>", "ceb353c43c594793"): 91.16e6}
+TRAFFIC = {("k_step2d_sgt<16,8,2,fwd>", "9498ac26b2994f47"): 82.00e6,
+           ("k_step2d_sgt<16,8,2,adj>", "9498ac26b2994f47"): 91.66e6,
+           ("k_step3d_tma<8,64,10,fwd>", "ff84bd7b5179962b"): 1434.45e6}
 
 
 def parse():
@@ -237,6 +238,7 @@ def config3_forward(dev, peak):
                         "200 of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
             "kernel": f"3D step variant {wave.wave_variant_count(2) and _variant3d()}", "avg_launch_us": avg * 1e6,
             "achieved_gbs": ach, "frac": ach / peak,
+            "traffic": TRAFFIC.get(("k_step3d_tma<8,64,10,fwd>", kernel_hash("k_step3d_tma"))),
             "bound": "hbm", "bytes_per_point": 16}
 
 
