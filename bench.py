@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--variants", default=None,
                     help="FWD,ADJ 2D kernel variants to use instead of running the autotuner")
+    ap.add_argument("--only-3d", type=int, default=0, metavar="NT",
+                    help="run only the config-3 3D forward for NT steps and print its line (for profiling)")
+    ap.add_argument("--variant-3d", type=int, default=-1, help="3D kernel variant (-1: library default)")
     return ap.parse_args()
 
 
@@ -212,14 +215,14 @@ def _variant3d():
     return "5 (k_step3d_tma<8,64,10>)"
 
 
-def config3_forward(dev, peak):
-    """3D config-3 forward (400 x 400 x 300 at 10 m, 160 000 receivers), 200 steps."""
+def config3_forward(dev, peak, nt: int = 200):
+    """3D config-3 forward (400 x 400 x 300 at 10 m, 160 000 receivers), nt steps."""
     import torch
 
     from paper_2304_05592_gb300 import synth, wave
     from paper_2304_05592_gb300.wave import Grid
 
-    p = synth.config3(nt=200)
+    p = synth.config3(nt=nt)
     g = Grid.of(p)
     v = torch.from_numpy(p.vel).to(dev)
     q = wave.wave_ricker(p.f0, p.dt, p.nt, device=dev)[None, :, None].contiguous()
@@ -235,7 +238,7 @@ def config3_forward(dev, peak):
     N = p.padded_points
     ach = 16 * N / avg / 1e9
     return {"workload": "3D forward 400x400x300 at 10 m + 40-cell sponge (480x480x380 padded), 160000 receivers, "
-                        "200 of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
+                        f"{p.nt} of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
             "kernel": f"3D step variant {wave.wave_variant_count(2) and _variant3d()}", "avg_launch_us": avg * 1e6,
             "achieved_gbs": ach, "frac": ach / peak,
             "traffic": TRAFFIC.get(("k_step3d_tma<8,64,10,fwd>", kernel_hash("k_step3d_tma"))),
@@ -343,6 +346,12 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
+    if args.only_3d:
+        from paper_2304_05592_gb300 import wave as _w
+
+        _w.wave_set_variant(2, args.variant_3d)
+        print(json.dumps({"config3_forward": config3_forward(dev, hbm_peak()[0], args.only_3d)}))
+        return 0
     from paper_2304_05592_gb300 import wave
     from paper_2304_05592_gb300.wave import Grid
 
