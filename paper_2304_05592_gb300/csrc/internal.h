@@ -146,8 +146,9 @@ constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile h
 // (kind 1) with tile height TZ, R rows per warp and NST stages, shot groups
 // (kind 2): one CTA runs its tile for G shots (R = thread rows), the
 // z-march (kind 3): one warp per TZ-row strip, R warps per CTA, prefetch
-// distance NST rows, shot groups fed by TMA (kind 4, fields as kind 2; NST = 1:
-// the previous level's tile comes by TMA too), or
+// distance NST rows, shot groups fed by TMA (kind 4, fields as kind 2; NST bit
+// 0: the previous level's tile comes by TMA too, bit 1: the sponge factors sit
+// in shared memory instead of registers), or
 // the persistent kernel over (tile, shot) items (kind 5, R = thread rows).
 // With kinds 2 and 4 in the adjoint, the gradient buffer holds one
 // accumulator per shot group; with kind 5, one per CTA segment of a tile.

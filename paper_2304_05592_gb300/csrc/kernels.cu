@@ -545,10 +545,12 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
 // stencil arithmetic, one load of the previous level and one store per 4
 // points.  Waits on the ring are bounded; on a timeout the CTA records
 // kErrTimeout, lets its issued copies land and returns.
-template <int TZ, int BZ, int G, bool PT, bool ADJ>
-__global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ))
+template <int TZ, int BZ, int G, int FL, bool ADJ>
+__global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ)))
     k_step2d_sgt(const __grid_constant__ StepMaps mp, const StepArgs a)
 {
+    constexpr bool PT = (FL & 1) != 0;  // the previous level's tile comes by TMA
+    constexpr bool SE = (FL & 2) != 0;  // sponge factors kept in shared memory, not registers
     constexpr int SW = kTX + 8;
     constexpr int RB = TZ / BZ;
     constexpr int SU = (TZ + 8) * SW;          // halo tile of u
@@ -557,7 +559,8 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
     extern __shared__ unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar[2];
     float* st = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
-    float* sg = st + 2 * SU2;  // [TZ][kTX] gradient tile (adjoint with imaging)
+    float* sg = st + 2 * SU2;                         // [TZ][kTX] gradient tile (adjoint with imaging)
+    float* se = sg + (ADJ ? TZ * kTX : 0);            // [2][TZ][kTX] eps and 1/(1+eps) (SE)
     const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
     const CUtensorMap* mt = ADJ ? &mp.tile_a : &mp.tile_f;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -584,7 +587,7 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
     int off[RB];
     bool live[RB], pad[RB];
     float4 kp[RB];
-    float eps[RB][4], inv[RB][4];
+    float eps[SE ? 1 : RB][4], inv[SE ? 1 : RB][4];
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
         const int gz = z0 + ty + rr * BZ;
@@ -593,11 +596,24 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
         pad[rr] = gz < a.Nz && nvalid <= 0 && gx < a.P;
         kp[rr] = live[rr] ? ld4(a.kap + off[rr]) : make_float4(0.f, 0.f, 0.f, 0.f);
         const int dz = sponge_depth(gz, a.nb, a.nz);
+        float ev[4], iv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
-            eps[rr][e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
-            inv[rr][e] = __frcp_rn(1.0f + eps[rr][e]);
+            ev[e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
+            iv[e] = __frcp_rn(1.0f + ev[e]);
+        }
+        if (SE) {
+            // each thread reads back only its own entries: no barrier needed
+            const int r = ty + rr * BZ;
+            *reinterpret_cast<float4*>(se + r * kTX + lx) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+            *reinterpret_cast<float4*>(se + (TZ + r) * kTX + lx) = make_float4(iv[0], iv[1], iv[2], iv[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                eps[SE ? 0 : rr][e] = ev[e];
+                inv[SE ? 0 : rr][e] = iv[e];
+            }
         }
     }
     float* gq = imaging ? a.gacc + (size_t)grp * a.cell : nullptr;
@@ -663,7 +679,13 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
             const float kv[4] = {kp[rr].x, kp[rr].y, kp[rr].z, kp[rr].w};
             const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
             float out[4];
-            update4(cen, um, lap, kv, eps[rr], inv[rr], zero4, out);
+            if (SE) {
+                const float4 E = lds4(se + r * kTX + lx), I = lds4(se + (TZ + r) * kTX + lx);
+                const float ev[4] = {E.x, E.y, E.z, E.w}, iv[4] = {I.x, I.y, I.z, I.w};
+                update4(cen, um, lap, kv, ev, iv, zero4, out);
+            } else {
+                update4(cen, um, lap, kv, eps[SE ? 0 : rr], inv[SE ? 0 : rr], zero4, out);
+            }
             // a full float4: points past Nx stay the zero exterior
             *reinterpret_cast<float4*>(un) = make_float4(out[0], nvalid > 1 ? out[1] : 0.0f,
                                                          nvalid > 2 ? out[2] : 0.0f, nvalid > 3 ? out[3] : 0.0f);
@@ -1779,14 +1801,16 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8}, {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4},
                                    {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2}, {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4},
                                    {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0}, {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2},
-                                   {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}};
+                                   {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}, {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2},
+                                   {4, 16, 8, 2, 4}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
                                    {1, 16, 1, 4, 0}, {2, 16, 8, 0, 8}, {2, 16, 8, 0, 16}, {2, 8, 8, 0, 8},
                                    {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
                                    {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}, {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0},
-                                   {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2}, {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}};
+                                   {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2}, {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4},
+                                   {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2}, {4, 16, 8, 2, 4}};
 // 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y, NST = ring
 // slots, G = 1 for the ring without block barriers): kind 0 is the z-march
 // with a shared-memory halo plane, kind 6 the TMA plane ring.
@@ -1873,17 +1897,18 @@ static void launch_2d_group(const StepArgs& a, cudaStream_t s)
     k_step2d_sg<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(a);
 }
 
-template <int TZ, int BZ, int G, bool ADJ, bool PT = false>
+template <int TZ, int BZ, int G, bool ADJ, int FL = 0>
 static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
-    constexpr size_t smem = (size_t)(2 * ((TZ + 8) * (kTX + 8) + (PT ? TZ * kTX : 0)) + (ADJ ? TZ * kTX : 0)) * 4 + 128;
+    constexpr size_t smem = (size_t)(2 * ((TZ + 8) * (kTX + 8) + ((FL & 1) ? TZ * kTX : 0)) + (ADJ ? TZ * kTX : 0) +
+                                     ((FL & 2) ? 2 * TZ * kTX : 0)) * 4 + 128;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, PT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, FL, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
     dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
-    k_step2d_sgt<TZ, BZ, G, PT, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
+    k_step2d_sgt<TZ, BZ, G, FL, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
 }
 
 template <int TZ, int BZ, bool ADJ>
@@ -1984,9 +2009,12 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 24: launch_2d_persistent<16, 8, false>(a, maps, s); break;
             case 25: launch_2d_persistent<8, 8, false>(a, maps, s); break;
             case 26: launch_2d_persistent<32, 8, false>(a, maps, s); break;
-            case 27: launch_2d_group_tma<16, 8, 2, false, true>(a, maps, s); break;
-            case 28: launch_2d_group_tma<16, 8, 4, false, true>(a, maps, s); break;
-            case 29: launch_2d_group_tma<8, 8, 4, false, true>(a, maps, s); break;
+            case 27: launch_2d_group_tma<16, 8, 2, false, 1>(a, maps, s); break;
+            case 28: launch_2d_group_tma<16, 8, 4, false, 1>(a, maps, s); break;
+            case 29: launch_2d_group_tma<8, 8, 4, false, 1>(a, maps, s); break;
+            case 30: launch_2d_group_tma<16, 8, 2, false, 2>(a, maps, s); break;
+            case 31: launch_2d_group_tma<16, 8, 2, false, 3>(a, maps, s); break;
+            case 32: launch_2d_group_tma<16, 8, 4, false, 2>(a, maps, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -2015,9 +2043,12 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 22: launch_2d_persistent<16, 8, true>(a, maps, s); break;
             case 23: launch_2d_persistent<8, 8, true>(a, maps, s); break;
             case 24: launch_2d_persistent<32, 8, true>(a, maps, s); break;
-            case 25: launch_2d_group_tma<16, 8, 2, true, true>(a, maps, s); break;
-            case 26: launch_2d_group_tma<16, 8, 4, true, true>(a, maps, s); break;
-            case 27: launch_2d_group_tma<8, 8, 4, true, true>(a, maps, s); break;
+            case 25: launch_2d_group_tma<16, 8, 2, true, 1>(a, maps, s); break;
+            case 26: launch_2d_group_tma<16, 8, 4, true, 1>(a, maps, s); break;
+            case 27: launch_2d_group_tma<8, 8, 4, true, 1>(a, maps, s); break;
+            case 28: launch_2d_group_tma<16, 8, 2, true, 2>(a, maps, s); break;
+            case 29: launch_2d_group_tma<16, 8, 2, true, 3>(a, maps, s); break;
+            case 30: launch_2d_group_tma<16, 8, 4, true, 2>(a, maps, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }
