@@ -94,6 +94,18 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
                           const float* M, int m_trans, const float* bias, const float* T, const float* table,
                           int act, float* pre, void* out, int out_bf16, void* stream);
 
+/* With the tensor cores allowed (fno_set_tensor_cores(1)), fno_combine runs
+ * on them (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory)
+ * when in and out are bf16, pre is NULL, m_trans = 0, Ci = 32 and Co is 32 or
+ * 64 -- the BF16 inference path of the Fourier layers and the first
+ * projection; the weights, the table and the spectral coefficients are rounded
+ * to BF16 on their way into shared memory.  fno_set_tensor_cores(0) keeps the
+ * CUDA-core kernel everywhere.  fno_tensor_core_status synchronises the device,
+ * returns WAVE_ERR_TIMEOUT if a tensor-core launch since the last call gave up
+ * waiting for its MMAs (its results are then invalid), and clears the flag. */
+wave_status_t fno_set_tensor_cores(int on);
+wave_status_t fno_tensor_core_status(void);
+
 /* Weight gradients of a pointwise layer: dM[o][i] = sum_{b,p} dU[b][o][p] in[b][i][p],
  * dbias[o] = sum_{b,p} dU[b][o][p] (npix = Nz Nx pixels per sample), both
  * overwritten.  `work` holds fno_wgrad_work_floats(B, Ci, Co, npix) floats;

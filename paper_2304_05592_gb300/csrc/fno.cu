@@ -286,6 +286,200 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
     }
 }
 
+// --- the same channel mix on the 5th-generation tensor cores (BF16 inference) -----------
+// One CTA (4 warps) computes a 128-pixel piece of one row (b, z) for all co
+// outputs as D[128 x co] = A1 B1^T + A2 B2^T with tcgen05.mma (kind::f16, BF16
+// operands, FP32 accumulator in tensor memory):
+//   A1[p][i] = in[b][i][z][x0+p]        B1[o][i] = M[o][i]
+//   A2[p][k] = table[x0+p][k]           B2[o][k] = (T re, -T im)[b][o][z][k]
+// (k = 2 kx + {0, 1}), so that A2 B2^T is the x part of the spectral inverse.
+// All four operands are staged in shared memory K-major without swizzle:
+// element (r, k) at (r/8)*512 + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes, i.e. core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along K (the descriptor's
+// leading offset) and 512 bytes apart along rows (its stride offset).  One
+// thread issues the MMAs (K = 16 each, two per operand pair) and commits them
+// to an mbarrier; each warp then reads its 32 accumulator lanes (= pixels) with
+// tcgen05.ld, adds the bias, applies GELU and stores BF16.  Requires ci = 32,
+// co in {32, 64}, mx <= 16.
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+{
+    // start address, leading (K) offset 128 B, stride (row-group) offset 512 B,
+    // descriptor version 1, no swizzle
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ uint4 pack8_bf16(const float* f)
+{
+    uint4 u;
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(f[0], f[1]), h1 = __floats2bfloat162_rn(f[2], f[3]),
+                   h2 = __floats2bfloat162_rn(f[4], f[5]), h3 = __floats2bfloat162_rn(f[6], f[7]);
+    u.x = *reinterpret_cast<uint32_t*>(&h0);
+    u.y = *reinterpret_cast<uint32_t*>(&h1);
+    u.z = *reinterpret_cast<uint32_t*>(&h2);
+    u.w = *reinterpret_cast<uint32_t*>(&h3);
+    return u;
+}
+
+constexpr int kTcCi = 32;
+
+// Set by the tensor-core combine if its wait for the MMAs gives up; read and
+// cleared by fno_tensor_core_status.
+__device__ int g_tc_err;
+
+template <int CO>
+__global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, const __nv_bfloat16* __restrict__ in,
+                                                    const float* __restrict__ M, const float* __restrict__ bias,
+                                                    const float* __restrict__ T, const float* __restrict__ tab,
+                                                    int act, __nv_bfloat16* __restrict__ out)
+{
+    __shared__ __align__(1024) unsigned char sA1[128 * kTcCi * 2];
+    __shared__ __align__(1024) unsigned char sA2[128 * 32 * 2];
+    __shared__ __align__(1024) unsigned char sB1[CO * kTcCi * 2];
+    __shared__ __align__(1024) unsigned char sB2[CO * 32 * 2];
+    __shared__ float sbias[CO];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.z, z = blockIdx.y, x0 = blockIdx.x * 128;
+    const int x = x0 + tid;
+    const bool xin = x < Nx;
+    const size_t npix = (size_t)Nz * Nx, pix = (size_t)z * Nx + x;
+    const int n2 = 2 * mx;
+    const bool spectral = T != nullptr;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"((uint32_t)CO)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // A1: this thread's pixel, all input channels
+    {
+        float f[kTcCi];
+#pragma unroll
+        for (int i = 0; i < kTcCi; ++i) f[i] = xin ? __bfloat162float(in[((size_t)b * kTcCi + i) * npix + pix]) : 0.0f;
+#pragma unroll
+        for (int kg = 0; kg < kTcCi / 8; ++kg)
+            *reinterpret_cast<uint4*>(sA1 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
+    }
+    if (spectral) {
+        // A2: the table factors of this thread's x; B2: the row's spectral coefficients
+        float f[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) f[k] = (xin && k < n2) ? tab[(size_t)x * n2 + k] : 0.0f;
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg)
+            *reinterpret_cast<uint4*>(sA2 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
+        for (int e = tid; e < CO * 4; e += 128) {
+            const int o = e >> 2, kg = e & 3;
+            float g[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 8 * kg + j;
+                const float t = k < n2 ? T[(((size_t)b * CO + o) * Nz + z) * n2 + k] : 0.0f;
+                g[j] = (k & 1) ? -t : t;
+            }
+            *reinterpret_cast<uint4*>(sB2 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
+        }
+    }
+    for (int e = tid; e < CO * 4; e += 128) {
+        const int o = e >> 2, kg = e & 3;
+        float g[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] = M[(size_t)o * kTcCi + 8 * kg + j];
+        *reinterpret_cast<uint4*>(sB1 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
+    }
+    for (int o = tid; o < CO; o += 128) sbias[o] = bias ? bias[o] : 0.0f;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tm = tmem_base;
+    if (tid == 0) {
+        // M = 128, N = CO, BF16 A and B (K-major), FP32 accumulator
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+#pragma unroll
+        for (int j = 0; j < kTcCi / 16; ++j)
+            umma_bf16(tm, umma_desc(su32(sA1) + j * 256), umma_desc(su32(sB1) + j * 256), idesc, j > 0);
+        if (spectral) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                umma_bf16(tm, umma_desc(su32(sA2) + j * 256), umma_desc(su32(sB2) + j * 256), idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar))
+                     : "memory");
+    }
+    bool ok = false;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(su32(&bar)), "r"(0u)
+            : "memory");
+        ok = done != 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const uint32_t ta = tm + ((uint32_t)(warp * 32) << 16);
+        const int p = warp * 32 + lane;  // the accumulator lane this thread reads = its pixel in the tile
+        const int xp = x0 + p;
+#pragma unroll
+        for (int half = 0; half < CO / 32; ++half) {
+            float v[32];
+            tmem_ld32(ta + half * 32, v);
+            if (xp < Nx) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int o = half * 32 + c;
+                    const float r = v[c] + sbias[o];
+                    out[((size_t)b * CO + o) * npix + (size_t)z * Nx + xp] =
+                        __float2bfloat16_rn(act == FNO_ACT_GELU ? gelu(r) : r);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(&g_tc_err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"((uint32_t)CO) : "memory");
+}
+
 // --- weight gradients ---------------------------------------------------------------
 // Block k sums its pixel range into partial[k][o][0..cip) (column ci is the
 // bias, fed by a constant 1); k_wgrad_reduce adds the blocks in index order.
@@ -425,6 +619,8 @@ __global__ void k_adam(long long n, float* __restrict__ p, const float* __restri
     }
 }
 
+int g_tensor_cores = 0;  // fno_combine's BF16 path uses tcgen05 when set and the shape allows
+
 wave_status_t launched()
 {
     const cudaError_t e = cudaGetLastError();
@@ -558,6 +754,16 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
     if (Nz > 65535 || B > 65535) return WAVE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int mxe = T ? mx : 1;
+    if (g_tensor_cores && in_bf16 && out_bf16 && !pre && !m_trans && Ci == kTcCi && (Co == 32 || Co == 64)) {
+        dim3 grid((Nx + 127) / 128, Nz, B);
+        if (Co == 32)
+            k_combine_tc<32><<<grid, 128, 0, s>>>(Nz, Nx, mxe, static_cast<const __nv_bfloat16*>(in), M, bias, T, table,
+                                                  act, static_cast<__nv_bfloat16*>(out));
+        else
+            k_combine_tc<64><<<grid, 128, 0, s>>>(Nz, Nx, mxe, static_cast<const __nv_bfloat16*>(in), M, bias, T, table,
+                                                  act, static_cast<__nv_bfloat16*>(out));
+        return launched();
+    }
     if (in_bf16 && out_bf16)
         combine_dispatch<__nv_bfloat16, __nv_bfloat16>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre,
                                                        out, s);
@@ -568,6 +774,23 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
     else
         combine_dispatch<float, float>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre, out, s);
     return launched();
+}
+
+wave_status_t fno_set_tensor_cores(int on)
+{
+    if (on != 0 && on != 1) return WAVE_ERR_ARG;
+    g_tensor_cores = on;
+    return WAVE_OK;
+}
+
+wave_status_t fno_tensor_core_status(void)
+{
+    int h = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_tc_err, sizeof(int)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int)) != cudaSuccess)
+        return WAVE_ERR_CUDA;
+    return h ? WAVE_ERR_TIMEOUT : WAVE_OK;
 }
 
 size_t fno_wgrad_work_floats(int B, int Ci, int Co, long long npix)

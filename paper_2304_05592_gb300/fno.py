@@ -51,6 +51,10 @@ def _lib():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = I
+        lib.fno_set_tensor_cores.argtypes = [I]
+        lib.fno_set_tensor_cores.restype = I
+        lib.fno_tensor_core_status.argtypes = []
+        lib.fno_tensor_core_status.restype = I
         lib.fno_wgrad_work_floats.argtypes = [I, I, I, L]
         lib.fno_wgrad_work_floats.restype = ctypes.c_size_t
         _BOUND = True
@@ -130,6 +134,16 @@ def fno_combine(inp, M, Co, m_trans=False, bias=None, T=None, table=None, mx=1, 
     _call("fno_combine", B, Ci, Co, Nz, Nx, mx, _p(inp), int(inp.dtype == torch.bfloat16), _p(M), int(m_trans),
           _p(bias), _p(T), _p(table), act, _p(pre), _p(out), int(out.dtype == torch.bfloat16), _s(stream))
     return out
+
+
+def fno_set_tensor_cores(on: bool):
+    """Allow or forbid the tcgen05 path of fno_combine's BF16 inference."""
+    _call("fno_set_tensor_cores", int(bool(on)))
+
+
+def fno_tensor_core_status() -> int:
+    """0, or 6 (WAVE_ERR_TIMEOUT) if a tensor-core launch gave up since the last call."""
+    return int(_lib().fno_tensor_core_status())
 
 
 def fno_wgrad_work_floats(B, Ci, Co, npix) -> int:
