@@ -271,7 +271,11 @@ def fno_preconditioner(dev):
 
     t_train = timed(lambda: net.train_step(x, y, 1e-4), 10)
     t_f32 = timed(lambda: net.forward(x, train=False), 20)
+    fno.fno_set_tensor_cores(False)
+    t_b16_cc = timed(lambda: net.forward(x, train=False, bf16=True), 20)
+    fno.fno_set_tensor_cores(True)
     t_b16 = timed(lambda: net.forward(x, train=False, bf16=True), 20)
+    tc_status = fno.fno_tensor_core_status()
     # algorithmic FLOPs of one forward per pixel: per layer 2 W^2 (channel mix) + 2 W 2mx (x transform)
     # + 2 W 2mx (inverse in the fused kernel) + 16 W KZ mx Nz / (Nz Nx) (z transforms) + 8 W^2 KZ mx / (Nz Nx)
     # (mode mix); lift 2 cin W; projection 2 W H + 2 H
@@ -283,7 +287,9 @@ def fno_preconditioner(dev):
     ach = flop * B / t_f32 / 1e12
     return {"workload": "FNO 4 layers, width 32, hidden 64, 16x16 modes, 256x512, batch 8",
             "train_samples_per_s": B / t_train, "infer_samples_per_s_fp32": B / t_f32,
-            "infer_samples_per_s_bf16_activations": B / t_b16, "forward_gflop_per_sample": flop / 1e9,
+            "infer_samples_per_s_bf16_tensor_cores": B / t_b16,
+            "infer_samples_per_s_bf16_cuda_cores": B / t_b16_cc, "tensor_core_status": tc_status,
+            "bf16_tensor_core_forward_tflops": flop * B / t_b16 / 1e12, "forward_gflop_per_sample": flop / 1e9,
             "forward_roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                                  "frac": ach / alu_peak, "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}}
 

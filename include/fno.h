@@ -94,7 +94,7 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
                           const float* M, int m_trans, const float* bias, const float* T, const float* table,
                           int act, float* pre, void* out, int out_bf16, void* stream);
 
-/* With the tensor cores allowed (fno_set_tensor_cores(1)), fno_combine runs
+/* With the tensor cores allowed (fno_set_tensor_cores(1), the default), fno_combine runs
  * on them (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory)
  * when in and out are bf16, pre is NULL, m_trans = 0, Ci = 32 and Co is 32 or
  * 64 -- the BF16 inference path of the Fourier layers and the first

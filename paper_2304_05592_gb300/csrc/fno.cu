@@ -619,7 +619,7 @@ __global__ void k_adam(long long n, float* __restrict__ p, const float* __restri
     }
 }
 
-int g_tensor_cores = 0;  // fno_combine's BF16 path uses tcgen05 when set and the shape allows
+int g_tensor_cores = 1;  // fno_combine's BF16 path uses tcgen05 when set and the shape allows
 
 wave_status_t launched()
 {

@@ -137,7 +137,7 @@ def fno_combine(inp, M, Co, m_trans=False, bias=None, T=None, table=None, mx=1, 
 
 
 def fno_set_tensor_cores(on: bool):
-    """Allow or forbid the tcgen05 path of fno_combine's BF16 inference."""
+    """Allow (the default) or forbid the tcgen05 path of fno_combine's BF16 inference."""
     _call("fno_set_tensor_cores", int(bool(on)))
 
 

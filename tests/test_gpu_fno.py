@@ -172,3 +172,37 @@ def test_training_reduces_loss():
         net.train_step(X[sel].contiguous(), T[sel].contiguous(), 3e-3)
     l1 = net.loss(X, T)
     assert l1 < 0.2 * l0, (l0, l1)
+
+
+@pytest.mark.parametrize("co,spectral", [(32, True), (64, False), (32, False)])
+def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral):
+    """The tcgen05 channel mix (BF16 operands, FP32 accumulation in tensor
+    memory) against the CUDA-core kernel and an FP64 reference computed from the
+    same BF16 activations, on a row length that leaves a ragged 128-pixel tile."""
+    B, ci, Nz, Nx, mz, mx = 2, 32, 12, 300, 4, 7
+    x = torch.from_numpy(RNG.standard_normal((B, ci, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
+    M, b = RNG.standard_normal((co, ci)) / np.sqrt(ci), RNG.standard_normal(co)
+    (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, mz, mx)
+    T = dev(RNG.standard_normal((B * co, Nz, mx, 2)) * 50.0) if spectral else None
+    kw = dict(bias=dev(b), act=fno.ACT_GELU, out_dtype=torch.bfloat16)
+    if spectral:
+        kw.update(T=T, table=ti, mx=mx)
+    try:
+        fno.fno_set_tensor_cores(True)
+        out_tc = fno.fno_combine(x, dev(M), co, **kw).float().cpu().numpy()
+        assert fno.fno_tensor_core_status() == 0
+        fno.fno_set_tensor_cores(False)
+        out_cc = fno.fno_combine(x, dev(M), co, **kw).float().cpu().numpy()
+    finally:
+        fno.fno_set_tensor_cores(True)
+    xf = x.float().cpu().numpy().astype(np.float64)
+    pre = ofno.pointwise(M, b, xf)
+    if spectral:
+        Tn = T.cpu().numpy().astype(np.float64).reshape(B, co, Nz, mx, 2)
+        tab = ti.cpu().numpy().astype(np.float64)
+        pre += np.einsum("bozk,xk->bozx", Tn[..., 0], tab[..., 0]) - np.einsum("bozk,xk->bozx", Tn[..., 1], tab[..., 1])
+    ref = ofno.gelu(pre)
+    # BF16 operands and output: relative errors of a few 1e-3
+    assert rel(out_tc, ref) < 1e-2, rel(out_tc, ref)
+    assert rel(out_cc, ref) < 1e-2, rel(out_cc, ref)
+    assert rel(out_tc, out_cc) < 1e-2
