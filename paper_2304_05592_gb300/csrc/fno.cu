@@ -480,6 +480,132 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"((uint32_t)CO) : "memory");
 }
 
+// x transform on the tensor cores (BF16 input): D[128 rows x 32] = A B^T with
+// A[r][x] = in[r0 + r][x] and B[n][x] = table[x][n] (zero for n >= 2 mx), K = Nx
+// in chunks of 64 staged K-major (stride offset 1024 B between 8-row groups)
+// into two alternating buffers; the MMAs of a chunk are committed to that
+// buffer's mbarrier, which is waited on before the buffer is refilled.
+constexpr int kTcKc = 64;
+
+__device__ __forceinline__ uint64_t umma_desc_sbo(uint32_t saddr, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(128) k_dft_x_tc(long long rows, int Nx, int n2, const __nv_bfloat16* __restrict__ in,
+                                                  const float* __restrict__ tab, float* __restrict__ out)
+{
+    constexpr int SA = 128 * kTcKc * 2, SB = 32 * kTcKc * 2;  // bytes per buffer
+    __shared__ __align__(1024) unsigned char sA[2][SA];
+    __shared__ __align__(1024) unsigned char sB[2][SB];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long r0 = (long long)blockIdx.x * 128;
+    const long long row = r0 + tid;
+    const bool rin = row < rows;
+    const int nchunk = (Nx + kTcKc - 1) / kTcKc;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(su32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    bool ok = true;
+    uint32_t tm = 0;
+    for (int c = 0; c < nchunk; ++c) {
+        const int buf = c & 1, k0 = c * kTcKc;
+        if (c >= 2) ok = mbar_wait_parity(&bar[buf], (uint32_t)((c - 2) >> 1) & 1u) && ok;  // MMAs of chunk c-2 done
+        // A: 128 rows x 64 x values
+        if ((Nx & 7) == 0) {
+            // 16-byte pieces, consecutive threads along a row (coalesced), copied as they are
+            for (int e = tid; e < 128 * (kTcKc / 8); e += 128) {
+                const int rr = e >> 3, kg = e & 7;
+                const long long gr = r0 + rr;
+                const int xk = k0 + 8 * kg;
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (gr < rows && xk < Nx) val = *reinterpret_cast<const uint4*>(in + gr * Nx + xk);
+                *reinterpret_cast<uint4*>(sA[buf] + (rr >> 3) * 1024 + kg * 128 + (rr & 7) * 16) = val;
+            }
+        } else {
+            for (int kg = 0; kg < kTcKc / 8; ++kg) {
+                float f[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int xk = k0 + 8 * kg + j;
+                    f[j] = (rin && xk < Nx) ? __bfloat162float(in[row * Nx + xk]) : 0.0f;
+                }
+                *reinterpret_cast<uint4*>(sA[buf] + (tid >> 3) * 1024 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f);
+            }
+        }
+        // B: 32 outputs x 64 x values of the table
+        for (int e = tid; e < 32 * (kTcKc / 8); e += 128) {
+            const int n = e & 31, kg = e >> 5;
+            float g[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int xk = k0 + 8 * kg + j;
+                g[j] = (n < n2 && xk < Nx) ? tab[(size_t)xk * n2 + n] : 0.0f;
+            }
+            *reinterpret_cast<uint4*>(sB[buf] + (n >> 3) * 1024 + kg * 128 + (n & 7) * 16) = pack8_bf16(g);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tm = tmem_base;
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < kTcKc / 16; ++j)
+                umma_bf16(tm, umma_desc_sbo(su32(sA[buf]) + j * 256, 1024), umma_desc_sbo(su32(sB[buf]) + j * 256, 1024),
+                          idesc, (c > 0 || j > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&bar[buf]))
+                         : "memory");
+        }
+    }
+    // the last chunk's commit covers all earlier MMAs
+    {
+        const int c = nchunk - 1;
+        ok = mbar_wait_parity(&bar[c & 1], (uint32_t)(c >> 1) & 1u) && ok;
+        if (nchunk >= 2) ok = mbar_wait_parity(&bar[(c - 1) & 1], (uint32_t)((c - 1) >> 1) & 1u) && ok;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        float v[32];
+        tmem_ld32(tm + ((uint32_t)(warp * 32) << 16), v);
+        const long long r = r0 + warp * 32 + lane;
+        if (r < rows)
+            for (int n = 0; n < n2; ++n) out[r * n2 + n] = v[n];
+    } else if (tid == 0) {
+        atomicOr(&g_tc_err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tm) : "memory");
+}
+
 // --- weight gradients ---------------------------------------------------------------
 // Block k sums its pixel range into partial[k][o][0..cip) (column ci is the
 // bias, fed by a constant 1); k_wgrad_reduce adds the blocks in index order.
@@ -619,6 +745,8 @@ __global__ void k_adam(long long n, float* __restrict__ p, const float* __restri
     }
 }
 
+long long nblk128(long long rows) { return (rows + 127) / 128; }
+
 int g_tensor_cores = 1;  // fno_combine's BF16 path uses tcgen05 when set and the shape allows
 
 wave_status_t launched()
@@ -683,6 +811,11 @@ wave_status_t fno_dft_x(long long rows, int Nx, int mx, const void* in, int in_b
     const long long nblk = (rows + kDxRows - 1) / kDxRows;
     if (nblk > 0x7fffffffLL) return WAVE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (in_bf16 && g_tensor_cores) {
+        k_dft_x_tc<<<(unsigned)nblk128(rows), 128, 0, s>>>(rows, Nx, 2 * mx, static_cast<const __nv_bfloat16*>(in),
+                                                           table, out);
+        return launched();
+    }
     if (in_bf16)
         k_dft_x<__nv_bfloat16><<<(unsigned)nblk, 256, 0, s>>>(rows, Nx, 2 * mx, static_cast<const __nv_bfloat16*>(in),
                                                               table, out);

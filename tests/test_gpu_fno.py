@@ -206,3 +206,25 @@ def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral):
     assert rel(out_tc, ref) < 1e-2, rel(out_tc, ref)
     assert rel(out_cc, ref) < 1e-2, rel(out_cc, ref)
     assert rel(out_tc, out_cc) < 1e-2
+
+
+@pytest.mark.parametrize("shape", [(2, 32, 24, 512, 16), (3, 5, 37, 300, 7)])
+def test_tensor_core_x_transform_matches_reference(shape):
+    """The tcgen05 x transform of BF16 activations (K = Nx in chunks of 64,
+    ragged K and rows) against the CUDA-core kernel and an FP64 reference."""
+    B, C, Nz, Nx, mx = shape
+    v = torch.from_numpy(RNG.standard_normal((B, C, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
+    (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, 4, mx)
+    try:
+        fno.fno_set_tensor_cores(True)
+        out_tc = fno.fno_dft_x(v, mx, tf).cpu().numpy()
+        assert fno.fno_tensor_core_status() == 0
+        fno.fno_set_tensor_cores(False)
+        out_cc = fno.fno_dft_x(v, mx, tf).cpu().numpy()
+    finally:
+        fno.fno_set_tensor_cores(True)
+    vf = v.float().cpu().numpy().astype(np.float64).reshape(-1, Nx)
+    tab = tf.cpu().numpy().astype(np.float64).reshape(Nx, 2 * mx)
+    ref = vf @ tab
+    assert rel(out_tc.reshape(ref.shape), ref) < 1e-2
+    assert rel(out_cc.reshape(ref.shape), ref) < 1e-5
