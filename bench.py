@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--only-3d", type=int, default=0, metavar="NT",
                     help="run only the config-3 3D forward for NT steps and print its line (for profiling)")
     ap.add_argument("--variant-3d", type=int, default=-1, help="3D kernel variant (-1: library default)")
+    ap.add_argument("--only-fno", action="store_true",
+                    help="run only the FNO training/inference measurement and print its line (for profiling)")
     return ap.parse_args()
 
 
@@ -352,6 +354,9 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
+    if args.only_fno:
+        print(json.dumps({"fno_preconditioner": fno_preconditioner(dev)}))
+        return 0
     if args.only_3d:
         from paper_2304_05592_gb300 import wave as _w
 

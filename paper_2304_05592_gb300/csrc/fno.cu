@@ -349,7 +349,22 @@ __device__ __forceinline__ uint4 pack8_bf16(const float* f)
     return u;
 }
 
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 constexpr int kTcCi = 32;
+constexpr int kTcRows = 8;  // rows (z) per CTA of the tensor-core combine
 
 // Set by the tensor-core combine if its wait for the MMAs gives up; read and
 // cleared by fno_tensor_core_status.
@@ -361,20 +376,22 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
                                                     const float* __restrict__ T, const float* __restrict__ tab,
                                                     int act, __nv_bfloat16* __restrict__ out)
 {
+    constexpr int RW = kTcRows;
     __shared__ __align__(1024) unsigned char sA1[128 * kTcCi * 2];
     __shared__ __align__(1024) unsigned char sA2[128 * 32 * 2];
     __shared__ __align__(1024) unsigned char sB1[CO * kTcCi * 2];
     __shared__ __align__(1024) unsigned char sB2[CO * 32 * 2];
+    __shared__ __align__(16) __nv_bfloat16 sOut[CO][128 + 8];  // epilogue transpose, padded rows
     __shared__ float sbias[CO];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.z, z = blockIdx.y, x0 = blockIdx.x * 128;
-    const int x = x0 + tid;
-    const bool xin = x < Nx;
-    const size_t npix = (size_t)Nz * Nx, pix = (size_t)z * Nx + x;
+    const int b = blockIdx.z, x0 = blockIdx.x * 128;
+    const int z0 = blockIdx.y * RW, z1 = min(z0 + RW, Nz);
+    const size_t npix = (size_t)Nz * Nx;
     const int n2 = 2 * mx;
     const bool spectral = T != nullptr;
+    const bool vec = (Nx & 3) == 0;
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
@@ -386,35 +403,7 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // A1: this thread's pixel, all input channels
-    {
-        float f[kTcCi];
-#pragma unroll
-        for (int i = 0; i < kTcCi; ++i) f[i] = xin ? __bfloat162float(in[((size_t)b * kTcCi + i) * npix + pix]) : 0.0f;
-#pragma unroll
-        for (int kg = 0; kg < kTcCi / 8; ++kg)
-            *reinterpret_cast<uint4*>(sA1 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
-    }
-    if (spectral) {
-        // A2: the table factors of this thread's x; B2: the row's spectral coefficients
-        float f[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) f[k] = (xin && k < n2) ? tab[(size_t)x * n2 + k] : 0.0f;
-#pragma unroll
-        for (int kg = 0; kg < 4; ++kg)
-            *reinterpret_cast<uint4*>(sA2 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
-        for (int e = tid; e < CO * 4; e += 128) {
-            const int o = e >> 2, kg = e & 3;
-            float g[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int k = 8 * kg + j;
-                const float t = k < n2 ? T[(((size_t)b * CO + o) * Nz + z) * n2 + k] : 0.0f;
-                g[j] = (k & 1) ? -t : t;
-            }
-            *reinterpret_cast<uint4*>(sB2 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
-        }
-    }
+    // set up once per CTA: the weights, the table factors of this x range, the bias
     for (int e = tid; e < CO * 4; e += 128) {
         const int o = e >> 2, kg = e & 3;
         float g[8];
@@ -422,62 +411,118 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
         for (int j = 0; j < 8; ++j) g[j] = M[(size_t)o * kTcCi + 8 * kg + j];
         *reinterpret_cast<uint4*>(sB1 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
     }
+    if (spectral) {
+        const int x = x0 + tid;
+        float f[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) f[k] = (x < Nx && k < n2) ? tab[(size_t)x * n2 + k] : 0.0f;
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg)
+            *reinterpret_cast<uint4*>(sA2 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
+    }
     for (int o = tid; o < CO; o += 128) sbias[o] = bias ? bias[o] : 0.0f;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tm = tmem_base;
-    if (tid == 0) {
-        // M = 128, N = CO, BF16 A and B (K-major), FP32 accumulator
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+    bool ok = true;
+    uint32_t tm = 0;
+    // thread layout for staging the activations: 4 pixels x 8 channels each
+    const int px4 = 4 * (tid & 31), cg = tid >> 5;  // pixels px4..px4+3, channels 8 cg .. 8 cg + 7
+    for (int z = z0; z < z1; ++z) {
+        const int it = z - z0;
+        {
+            float f[4][8];
+            const int xs = x0 + px4;
 #pragma unroll
-        for (int j = 0; j < kTcCi / 16; ++j)
-            umma_bf16(tm, umma_desc(su32(sA1) + j * 256), umma_desc(su32(sB1) + j * 256), idesc, j > 0);
-        if (spectral) {
+            for (int j = 0; j < 8; ++j) {
+                const __nv_bfloat16* src = in + ((size_t)b * kTcCi + 8 * cg + j) * npix + (size_t)z * Nx;
+                if (vec && xs + 3 < Nx) {
+                    const uint2 u = *reinterpret_cast<const uint2*>(src + xs);
+                    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+                    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+                    f[0][j] = __low2float(lo);
+                    f[1][j] = __high2float(lo);
+                    f[2][j] = __low2float(hi);
+                    f[3][j] = __high2float(hi);
+                } else {
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
-                umma_bf16(tm, umma_desc(su32(sA2) + j * 256), umma_desc(su32(sB2) + j * 256), idesc, 1u);
+                    for (int q = 0; q < 4; ++q) f[q][j] = xs + q < Nx ? __bfloat162float(src[xs + q]) : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = px4 + q;
+                *reinterpret_cast<uint4*>(sA1 + (r >> 3) * 512 + cg * 128 + (r & 7) * 16) = pack8_bf16(f[q]);
+            }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar))
-                     : "memory");
-    }
-    bool ok = false;
-    for (int it = 0; it < (1 << 22) && !ok; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(su32(&bar)), "r"(0u)
-            : "memory");
-        ok = done != 0;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        const uint32_t ta = tm + ((uint32_t)(warp * 32) << 16);
-        const int p = warp * 32 + lane;  // the accumulator lane this thread reads = its pixel in the tile
-        const int xp = x0 + p;
+        if (spectral) {
+            for (int e = tid; e < CO * 4; e += 128) {
+                const int o = e >> 2, kg = e & 3;
+                float g[8];
 #pragma unroll
-        for (int half = 0; half < CO / 32; ++half) {
-            float v[32];
-            tmem_ld32(ta + half * 32, v);
-            if (xp < Nx) {
+                for (int j = 0; j < 8; ++j) {
+                    const int k = 8 * kg + j;
+                    const float t = k < n2 ? T[(((size_t)b * CO + o) * Nz + z) * n2 + k] : 0.0f;
+                    g[j] = (k & 1) ? -t : t;
+                }
+                *reinterpret_cast<uint4*>(sB2 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tm = tmem_base;
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < kTcCi / 16; ++j)
+                umma_bf16(tm, umma_desc(su32(sA1) + j * 256), umma_desc(su32(sB1) + j * 256), idesc, j > 0);
+            if (spectral) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    umma_bf16(tm, umma_desc(su32(sA2) + j * 256), umma_desc(su32(sB2) + j * 256), idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&bar))
+                         : "memory");
+        }
+        ok = mbar_wait_parity(&bar, (uint32_t)it & 1u) && ok;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+            const uint32_t ta = tm + ((uint32_t)(warp * 32) << 16);
+            const int p = warp * 32 + lane;  // accumulator lane = pixel of the tile
+#pragma unroll
+            for (int half = 0; half < CO / 32; ++half) {
+                float v[32];
+                tmem_ld32(ta + half * 32, v);
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
-                    const int o = half * 32 + c;
-                    const float r = v[c] + sbias[o];
-                    out[((size_t)b * CO + o) * npix + (size_t)z * Nx + xp] =
-                        __float2bfloat16_rn(act == FNO_ACT_GELU ? gelu(r) : r);
+                    const float r = v[c] + sbias[half * 32 + c];
+                    sOut[half * 32 + c][p] = __float2bfloat16_rn(act == FNO_ACT_GELU ? gelu(r) : r);
                 }
             }
         }
-    } else if (tid == 0) {
-        atomicOr(&g_tc_err, 1);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // accumulator read and staging buffers free before the next row
+        if (ok) {
+            // coalesced stores: a warp writes 128 pixels (4 per lane) of one output channel
+            for (int o = warp; o < CO; o += 4) {
+                const int xs = x0 + 4 * lane;
+                __nv_bfloat16* dst = out + ((size_t)b * CO + o) * npix + (size_t)z * Nx;
+                if (vec && xs + 3 < Nx) {
+                    *reinterpret_cast<uint2*>(dst + xs) = *reinterpret_cast<const uint2*>(&sOut[o][4 * lane]);
+                } else {
+                    for (int q = 0; q < 4; ++q)
+                        if (xs + q < Nx) dst[xs + q] = sOut[o][4 * lane + q];
+                }
+            }
+        }
+        __syncthreads();  // sOut read before the next row's epilogue
     }
+    if (!ok && tid == 0) atomicOr(&g_tc_err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"((uint32_t)CO) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)CO)
+                     : "memory");
 }
 
 // x transform on the tensor cores (BF16 input): D[128 rows x 32] = A B^T with
@@ -493,19 +538,6 @@ __device__ __forceinline__ uint64_t umma_desc_sbo(uint32_t saddr, uint32_t sbo)
            ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
-{
-    for (int it = 0; it < (1 << 22); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(su32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 __global__ void __launch_bounds__(128) k_dft_x_tc(long long rows, int Nx, int n2, const __nv_bfloat16* __restrict__ in,
                                                   const float* __restrict__ tab, float* __restrict__ out)
@@ -888,7 +920,7 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
     cudaStream_t s = (cudaStream_t)stream;
     const int mxe = T ? mx : 1;
     if (g_tensor_cores && in_bf16 && out_bf16 && !pre && !m_trans && Ci == kTcCi && (Co == 32 || Co == 64)) {
-        dim3 grid((Nx + 127) / 128, Nz, B);
+        dim3 grid((Nx + 127) / 128, (Nz + kTcRows - 1) / kTcRows, B);
         if (Co == 32)
             k_combine_tc<32><<<grid, 128, 0, s>>>(Nz, Nx, mxe, static_cast<const __nv_bfloat16*>(in), M, bias, T, table,
                                                   act, static_cast<__nv_bfloat16*>(out));

@@ -174,12 +174,13 @@ def test_training_reduces_loss():
     assert l1 < 0.2 * l0, (l0, l1)
 
 
-@pytest.mark.parametrize("co,spectral", [(32, True), (64, False), (32, False)])
-def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral):
+@pytest.mark.parametrize("co,spectral,Nx", [(32, True, 300), (64, False, 300), (32, False, 300), (32, True, 301)])
+def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nx):
     """The tcgen05 channel mix (BF16 operands, FP32 accumulation in tensor
     memory) against the CUDA-core kernel and an FP64 reference computed from the
-    same BF16 activations, on a row length that leaves a ragged 128-pixel tile."""
-    B, ci, Nz, Nx, mz, mx = 2, 32, 12, 300, 4, 7
+    same BF16 activations, on row lengths that leave a ragged 128-pixel tile
+    (one not a multiple of 4) and a ragged group of rows."""
+    B, ci, Nz, mz, mx = 2, 32, 12, 4, 7
     x = torch.from_numpy(RNG.standard_normal((B, ci, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
     M, b = RNG.standard_normal((co, ci)) / np.sqrt(ci), RNG.standard_normal(co)
     (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, mz, mx)
