@@ -287,20 +287,26 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
 }
 
 // --- the same channel mix on the 5th-generation tensor cores (BF16 inference) -----------
-// One CTA (4 warps) computes a 128-pixel piece of one row (b, z) for all co
-// outputs as D[128 x co] = A1 B1^T + A2 B2^T with tcgen05.mma (kind::f16, BF16
-// operands, FP32 accumulator in tensor memory):
+// One CTA (4 warps) computes 128-pixel pieces of rw consecutive rows (b, z) for
+// all co outputs, one row at a time, as D[128 x co] = A1 B1^T + A2 B2^T with
+// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory):
 //   A1[p][i] = in[b][i][z][x0+p]        B1[o][i] = M[o][i]
 //   A2[p][k] = table[x0+p][k]           B2[o][k] = (T re, -T im)[b][o][z][k]
 // (k = 2 kx + {0, 1}), so that A2 B2^T is the x part of the spectral inverse.
-// All four operands are staged in shared memory K-major without swizzle:
-// element (r, k) at (r/8)*512 + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes, i.e. core
-// matrices of 8 rows x 16 bytes, 128 bytes apart along K (the descriptor's
-// leading offset) and 512 bytes apart along rows (its stride offset).  One
-// thread issues the MMAs (K = 16 each, two per operand pair) and commits them
-// to an mbarrier; each warp then reads its 32 accumulator lanes (= pixels) with
-// tcgen05.ld, adds the bias, applies GELU and stores BF16.  Requires ci = 32,
-// co in {32, 64}, mx <= 16.
+// Operands sit in shared memory without swizzle, in core matrices of 8 rows x
+// 16 bytes: B1, A2 and B2 K-major (element (r, k) at (r/8)*512 + (k/8)*128 +
+// (r%8)*16 + (k%8)*2 bytes), A1 pixel-major (element (p, i) at (p/8)*512 +
+// (i/8)*128 + (i%8)*16 + (p%8)*2), which is how the activations lie in memory:
+// every 16-byte piece of 8 pixels of one channel is copied as it is
+// (cp.async) and the MMA reads A1 transposed.  In both layouts the
+// descriptor's leading offset (128 B) steps along K and its stride offset
+// (512 B) along rows.  Pipeline, for row it: row it+1's activations and T
+// arrived during row it-1; T is converted to BF16 and row it+1's MMAs go to
+// the second accumulator; row it's MMAs are waited for, row it+2's copies go
+// into the buffers row it has finished with, and row it's accumulator is read
+// (tcgen05.ld), biased, passed through GELU and stored BF16 through a shared
+// transpose so that each warp writes whole rows.  Requires ci = 32, co in
+// {32, 64}, mx <= 16.
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -363,47 +369,139 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
     return false;
 }
 
-constexpr int kTcCi = 32;
-constexpr int kTcRows = 8;  // rows (z) per CTA of the tensor-core combine
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Set by the tensor-core combine if its wait for the MMAs gives up; read and
+constexpr int kTcCi = 32;
+constexpr int kTcTs = 36;  // floats per row of the raw T buffer (32 + 4 of padding against bank conflicts)
+
+// Set by the tensor-core kernels if a wait for their MMAs gives up; read and
 // cleared by fno_tensor_core_status.
 __device__ int g_tc_err;
 
+// dynamic shared memory of k_combine_tc<CO>, in bytes (all pieces 16-byte aligned)
+__host__ __device__ constexpr int tc_smem_bytes(int co)
+{
+    return 2 * 8192 /*A1 x2*/ + 8192 /*A2*/ + co * 64 /*B1*/ + 2 * co * 64 /*B2 x2*/ + 2 * co * kTcTs * 4 /*raw T x2*/ +
+           co * (128 + 8) * 2 /*output transpose*/;
+}
+
 template <int CO>
-__global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, const __nv_bfloat16* __restrict__ in,
+__global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int rw, const __nv_bfloat16* __restrict__ in,
                                                     const float* __restrict__ M, const float* __restrict__ bias,
                                                     const float* __restrict__ T, const float* __restrict__ tab,
                                                     int act, __nv_bfloat16* __restrict__ out)
 {
-    constexpr int RW = kTcRows;
-    __shared__ __align__(1024) unsigned char sA1[128 * kTcCi * 2];
-    __shared__ __align__(1024) unsigned char sA2[128 * 32 * 2];
-    __shared__ __align__(1024) unsigned char sB1[CO * kTcCi * 2];
-    __shared__ __align__(1024) unsigned char sB2[CO * 32 * 2];
-    __shared__ __align__(16) __nv_bfloat16 sOut[CO][128 + 8];  // epilogue transpose, padded rows
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* const sA1 = smem;               // [2][8192]
+    unsigned char* const sA2 = smem + 2 * 8192;    // [8192]
+    unsigned char* const sB1 = sA2 + 8192;         // [CO * 64]
+    unsigned char* const sB2 = sB1 + CO * 64;      // [2][CO * 64]
+    float* const sT = reinterpret_cast<float*>(sB2 + 2 * CO * 64);  // [2][CO][kTcTs]
+    __nv_bfloat16(*const sOut)[128 + 8] = reinterpret_cast<__nv_bfloat16(*)[128 + 8]>(sT + 2 * CO * kTcTs);
     __shared__ float sbias[CO];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.z, x0 = blockIdx.x * 128;
-    const int z0 = blockIdx.y * RW, z1 = min(z0 + RW, Nz);
+    const int z0 = blockIdx.y * rw, nrows = min(rw, Nz - z0);
     const size_t npix = (size_t)Nz * Nx;
     const int n2 = 2 * mx;
     const bool spectral = T != nullptr;
-    const bool vec = (Nx & 3) == 0;
+    const bool vecA = (Nx & 7) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    const bool vecT = (n2 & 3) == 0 && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
+    if (nrows <= 0) return;  // uniform over the CTA
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
-                     "r"((uint32_t)CO)
+                     "r"((uint32_t)(2 * CO))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // set up once per CTA: the weights, the table factors of this x range, the bias
+
+    // row r of this CTA -> buffers `slot`: activations (pixel-major A1) and raw T
+    auto prefetch = [&](int r, int slot) {
+        const int z = z0 + r;
+        unsigned char* a = sA1 + slot * 8192;
+        if (vecA) {
+            // a quarter-warp copies one 8-pixel group of 8 channels: 128 contiguous bytes
+            // in shared memory, 16 bytes from each of 8 channel rows in global memory
+            const int g = tid >> 3, x = x0 + 8 * g;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = 8 * i + (tid & 7);
+                const __nv_bfloat16* src = in + ((size_t)b * kTcCi + c) * npix + (size_t)z * Nx + min(x, Nx - 8);
+                cp_async16(su32(a + g * 512 + i * 128 + (tid & 7) * 16), src, x < Nx ? 16 : 0);
+            }
+        } else {
+            for (int e = tid; e < kTcCi * 128; e += 128) {
+                const int c = e >> 7, p = e & 127, x = x0 + p;
+                const __nv_bfloat16 v =
+                    x < Nx ? in[((size_t)b * kTcCi + c) * npix + (size_t)z * Nx + x] : __float2bfloat16_rn(0.0f);
+                *reinterpret_cast<__nv_bfloat16*>(a + (p >> 3) * 512 + (c >> 3) * 128 + (c & 7) * 16 + (p & 7) * 2) = v;
+            }
+        }
+        if (spectral) {
+            float* t = sT + slot * CO * kTcTs;
+            if (vecT) {
+                for (int e = tid; e < CO * 8; e += 128) {
+                    const int o = e >> 3, j = e & 7;
+                    if (4 * j < n2) cp_async16(su32(t + o * kTcTs + 4 * j), T + (((size_t)b * CO + o) * Nz + z) * n2 + 4 * j, 16);
+                }
+            } else {
+                for (int e = tid; e < CO * 32; e += 128) {
+                    const int o = e >> 5, k = e & 31;
+                    if (k < n2) t[o * kTcTs + k] = T[(((size_t)b * CO + o) * Nz + z) * n2 + k];
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // raw T of buffers `slot` -> B2 (BF16, K-major, odd entries negated)
+    auto convert = [&](int slot) {
+        if (!spectral) return;
+        const float* t = sT + slot * CO * kTcTs;
+        unsigned char* bb = sB2 + slot * CO * 64;
+        for (int e = tid; e < CO * 4; e += 128) {
+            const int o = e % CO, kg = e / CO;
+            float g[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 8 * kg + j;
+                const float v = k < n2 ? t[o * kTcTs + k] : 0.0f;
+                g[j] = (k & 1) ? -v : v;
+            }
+            *reinterpret_cast<uint4*>(bb + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
+        }
+    };
+    const uint32_t idesc_k = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t idesc_a1 = idesc_k | (1u << 15);  // A read transposed (pixel-major)
+    auto issue = [&](int slot, uint32_t tm) {
+#pragma unroll
+        for (int j = 0; j < kTcCi / 16; ++j)
+            umma_bf16(tm, umma_desc(su32(sA1 + slot * 8192) + j * 256), umma_desc(su32(sB1) + j * 256), idesc_a1, j > 0);
+        if (spectral) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                umma_bf16(tm, umma_desc(su32(sA2) + j * 256), umma_desc(su32(sB2 + slot * CO * 64) + j * 256), idesc_k, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar[slot]))
+                     : "memory");
+    };
+
+    prefetch(0, 0);
+    if (nrows > 1) prefetch(1, 1);
+    // set up once per CTA while the first rows are in flight: weights, table, bias
     for (int e = tid; e < CO * 4; e += 128) {
         const int o = e >> 2, kg = e & 3;
         float g[8];
@@ -421,73 +519,36 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
             *reinterpret_cast<uint4*>(sA2 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
     }
     for (int o = tid; o < CO; o += 128) sbias[o] = bias ? bias[o] : 0.0f;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+    if (nrows > 1) cp_async_wait_prev();
+    else cp_async_wait_all();
+    __syncthreads();  // row 0's raw T visible to every thread
+    convert(0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tm = tmem_base;
+    if (tid == 0) issue(0, tm);
+
     bool ok = true;
-    uint32_t tm = 0;
-    // thread layout for staging the activations: 4 pixels x 8 channels each
-    const int px4 = 4 * (tid & 31), cg = tid >> 5;  // pixels px4..px4+3, channels 8 cg .. 8 cg + 7
-    for (int z = z0; z < z1; ++z) {
-        const int it = z - z0;
-        {
-            float f[4][8];
-            const int xs = x0 + px4;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const __nv_bfloat16* src = in + ((size_t)b * kTcCi + 8 * cg + j) * npix + (size_t)z * Nx;
-                if (vec && xs + 3 < Nx) {
-                    const uint2 u = *reinterpret_cast<const uint2*>(src + xs);
-                    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
-                    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
-                    f[0][j] = __low2float(lo);
-                    f[1][j] = __high2float(lo);
-                    f[2][j] = __low2float(hi);
-                    f[3][j] = __high2float(hi);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) f[q][j] = xs + q < Nx ? __bfloat162float(src[xs + q]) : 0.0f;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = px4 + q;
-                *reinterpret_cast<uint4*>(sA1 + (r >> 3) * 512 + cg * 128 + (r & 7) * 16) = pack8_bf16(f[q]);
-            }
+    for (int it = 0; it < nrows; ++it) {
+        const int cur = it & 1, nxt = cur ^ 1;
+        if (it + 1 < nrows) {
+            cp_async_wait_all();  // this thread's copies of row it+1
+            __syncthreads();
+            convert(nxt);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        if (spectral) {
-            for (int e = tid; e < CO * 4; e += 128) {
-                const int o = e >> 2, kg = e & 3;
-                float g[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int k = 8 * kg + j;
-                    const float t = k < n2 ? T[(((size_t)b * CO + o) * Nz + z) * n2 + k] : 0.0f;
-                    g[j] = (k & 1) ? -t : t;
-                }
-                *reinterpret_cast<uint4*>(sB2 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        __syncthreads();  // row it+1's operands complete; the previous row's stores have read sOut
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tm = tmem_base;
-        if (tid == 0) {
-#pragma unroll
-            for (int j = 0; j < kTcCi / 16; ++j)
-                umma_bf16(tm, umma_desc(su32(sA1) + j * 256), umma_desc(su32(sB1) + j * 256), idesc, j > 0);
-            if (spectral) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    umma_bf16(tm, umma_desc(su32(sA2) + j * 256), umma_desc(su32(sB2) + j * 256), idesc, 1u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(&bar))
-                         : "memory");
-        }
-        ok = mbar_wait_parity(&bar, (uint32_t)it & 1u) && ok;
+        if (it + 1 < nrows && tid == 0) issue(nxt, tm + (uint32_t)(nxt * CO));
+        ok = mbar_wait_parity(&bar[cur], (uint32_t)(it >> 1) & 1u) && ok;  // row it's MMAs are done
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (it + 2 < nrows) prefetch(it + 2, cur);  // into the buffers row it's MMAs have finished reading
         if (ok) {
-            const uint32_t ta = tm + ((uint32_t)(warp * 32) << 16);
+            const uint32_t ta = tm + (uint32_t)(cur * CO) + ((uint32_t)(warp * 32) << 16);
             const int p = warp * 32 + lane;  // accumulator lane = pixel of the tile
 #pragma unroll
             for (int half = 0; half < CO / 32; ++half) {
@@ -501,13 +562,13 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // accumulator read and staging buffers free before the next row
+        __syncthreads();  // sOut complete; row it's accumulator has been read
         if (ok) {
             // coalesced stores: a warp writes 128 pixels (4 per lane) of one output channel
+            const int z = z0 + it, xs = x0 + 4 * lane;
             for (int o = warp; o < CO; o += 4) {
-                const int xs = x0 + 4 * lane;
                 __nv_bfloat16* dst = out + ((size_t)b * CO + o) * npix + (size_t)z * Nx;
-                if (vec && xs + 3 < Nx) {
+                if ((Nx & 3) == 0 && xs + 3 < Nx) {
                     *reinterpret_cast<uint2*>(dst + xs) = *reinterpret_cast<const uint2*>(&sOut[o][4 * lane]);
                 } else {
                     for (int q = 0; q < 4; ++q)
@@ -515,13 +576,12 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, cons
                 }
             }
         }
-        __syncthreads();  // sOut read before the next row's epilogue
     }
     if (!ok && tid == 0) atomicOr(&g_tc_err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)CO)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"((uint32_t)(2 * CO))
                      : "memory");
 }
 
@@ -628,8 +688,11 @@ __global__ void __launch_bounds__(128) k_dft_x_tc(long long rows, int Nx, int n2
         float v[32];
         tmem_ld32(tm + ((uint32_t)(warp * 32) << 16), v);
         const long long r = r0 + warp * 32 + lane;
-        if (r < rows)
-            for (int n = 0; n < n2; ++n) out[r * n2 + n] = v[n];
+        if (r < rows) {
+#pragma unroll
+            for (int n = 0; n < 32; ++n)
+                if (n < n2) out[r * n2 + n] = v[n];
+        }
     } else if (tid == 0) {
         atomicOr(&g_tc_err, 1);
     }
@@ -807,6 +870,58 @@ void combine_launch(int B, int ci, int co, int Nz, int Nx, int mx, const void* i
                                                          T, tab, act, pre, static_cast<Tout*>(out));
 }
 
+// Resident CTAs of k_combine_tc<CO> on the whole device (per device, found
+// once), from the kernel's registers and shared memory against the SM's limits.
+template <int CO>
+int tc_slots()
+{
+    static int slots[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (slots[dev] == 0) {
+        cudaFuncAttributes fa;
+        int nsm = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0, thr_sm = 0;
+        // all of the unified L1 as shared memory
+        if (cudaFuncSetAttribute(k_combine_tc<CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(CO)) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_combine_tc<CO>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, k_combine_tc<CO>) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+            return 0;
+        const int smem_cta = tc_smem_bytes(CO) + (int)fa.sharedSizeBytes + smem_rsv;
+        const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+        int occ = std::min(smem_sm / smem_cta, thr_sm / 128);
+        if (regs_warp > 0) occ = std::min(occ, regs_sm / (4 * regs_warp));
+        // a CTA holds 2 CO columns of tensor memory out of 512
+        occ = std::min(occ, 512 / (2 * CO));
+        if (occ < 1) return 0;
+        slots[dev] = nsm * occ;
+    }
+    return slots[dev];
+}
+
+// One wave: rows per CTA so that the (x tiles) x (row chunks) x B grid fills
+// the resident slots once.
+template <int CO>
+wave_status_t combine_tc_launch(int B, int Nz, int Nx, int mx, const void* in, const float* M, const float* bias,
+                                const float* T, const float* tab, int act, void* out, cudaStream_t s)
+{
+    const int slots = tc_slots<CO>();
+    if (slots <= 0) return WAVE_ERR_CUDA;
+    const long long xt = (Nx + 127) / 128, tiles = xt * Nz * (long long)B;
+    int rw = (int)std::min<long long>(Nz, std::max<long long>(1, (tiles + slots - 1) / slots));
+    while (rw < Nz && xt * ((Nz + rw - 1) / rw) * B > slots) ++rw;  // rounding must not spill into a second wave
+    dim3 grid((unsigned)xt, (unsigned)((Nz + rw - 1) / rw), B);
+    k_combine_tc<CO><<<grid, 128, tc_smem_bytes(CO), s>>>(Nz, Nx, mx, rw, static_cast<const __nv_bfloat16*>(in), M, bias,
+                                                           T, tab, act, static_cast<__nv_bfloat16*>(out));
+    return launched();
+}
+
 template <typename Tin, typename Tout>
 void combine_dispatch(int B, int ci, int co, int Nz, int Nx, int mx, const void* in, const float* M, int mt,
                       const float* bias, const float* T, const float* tab, int act, float* pre, void* out,
@@ -920,14 +1035,9 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
     cudaStream_t s = (cudaStream_t)stream;
     const int mxe = T ? mx : 1;
     if (g_tensor_cores && in_bf16 && out_bf16 && !pre && !m_trans && Ci == kTcCi && (Co == 32 || Co == 64)) {
-        dim3 grid((Nx + 127) / 128, (Nz + kTcRows - 1) / kTcRows, B);
         if (Co == 32)
-            k_combine_tc<32><<<grid, 128, 0, s>>>(Nz, Nx, mxe, static_cast<const __nv_bfloat16*>(in), M, bias, T, table,
-                                                  act, static_cast<__nv_bfloat16*>(out));
-        else
-            k_combine_tc<64><<<grid, 128, 0, s>>>(Nz, Nx, mxe, static_cast<const __nv_bfloat16*>(in), M, bias, T, table,
-                                                  act, static_cast<__nv_bfloat16*>(out));
-        return launched();
+            return combine_tc_launch<32>(B, Nz, Nx, mxe, in, M, bias, T, table, act, out, s);
+        return combine_tc_launch<64>(B, Nz, Nx, mxe, in, M, bias, T, table, act, out, s);
     }
     if (in_bf16 && out_bf16)
         combine_dispatch<__nv_bfloat16, __nv_bfloat16>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre,

@@ -174,13 +174,17 @@ def test_training_reduces_loss():
     assert l1 < 0.2 * l0, (l0, l1)
 
 
-@pytest.mark.parametrize("co,spectral,Nx", [(32, True, 300), (64, False, 300), (32, False, 300), (32, True, 301)])
-def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nx):
+@pytest.mark.parametrize("co,spectral,Nz,Nx,mx", [
+    (32, True, 12, 300, 7), (64, False, 12, 300, 7), (32, False, 12, 300, 7), (32, True, 12, 301, 7),
+    # rows a multiple of 8 pixels and an even mode count: activations and T copied with cp.async;
+    # Nz = 301 gives several rows per CTA and a last CTA with a single row
+    (32, True, 301, 264, 8), (64, True, 301, 520, 16), (64, False, 40, 512, 16), (32, True, 301, 264, 7)])
+def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nz, Nx, mx):
     """The tcgen05 channel mix (BF16 operands, FP32 accumulation in tensor
     memory) against the CUDA-core kernel and an FP64 reference computed from the
     same BF16 activations, on row lengths that leave a ragged 128-pixel tile
-    (one not a multiple of 4) and a ragged group of rows."""
-    B, ci, Nz, mz, mx = 2, 32, 12, 4, 7
+    (some not a multiple of 4 or 8) and ragged groups of rows."""
+    B, ci, mz = 2, 32, 4
     x = torch.from_numpy(RNG.standard_normal((B, ci, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
     M, b = RNG.standard_normal((co, ci)) / np.sqrt(ci), RNG.standard_normal(co)
     (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, mz, mx)
@@ -201,7 +205,7 @@ def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nx):
     if spectral:
         Tn = T.cpu().numpy().astype(np.float64).reshape(B, co, Nz, mx, 2)
         tab = ti.cpu().numpy().astype(np.float64)
-        pre += np.einsum("bozk,xk->bozx", Tn[..., 0], tab[..., 0]) - np.einsum("bozk,xk->bozx", Tn[..., 1], tab[..., 1])
+        pre += Tn[..., 0] @ tab[..., 0].T - Tn[..., 1] @ tab[..., 1].T
     ref = ofno.gelu(pre)
     # BF16 operands and output: relative errors of a few 1e-3
     assert rel(out_tc, ref) < 1e-2, rel(out_tc, ref)
