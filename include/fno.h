@@ -94,11 +94,23 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
                           const float* M, int m_trans, const float* bias, const float* T, const float* table,
                           int act, float* pre, void* out, int out_bf16, void* stream);
 
+/* The projection head Q of the FNO (two pointwise layers, GELU between them)
+ * in one pass, for inference:
+ *   out[b][0][z][x] = q2 + sum_h Q2[h] GELU(q1[h] + sum_i Q1[h][i] in[b][i][z][x])
+ * with Q1 [H][Ci], q1 [H] (may be NULL), Q2 [1][H], q2 [1] (may be NULL); in is
+ * float or bf16 (in_bf16), out float [B][1][Nz][Nx].  The H hidden channels
+ * never leave the chip (fno_combine followed by a second fno_combine writes and
+ * reads them).  With bf16 input, Ci = 32 and H = 32 or 64 it runs on the
+ * tensor cores (the hidden layer as in fno_combine, the second layer in the
+ * epilogue in float), otherwise on the CUDA cores. */
+wave_status_t fno_project(int B, int Ci, int H, int Nz, int Nx, const void* in, int in_bf16, const float* Q1,
+                          const float* q1, const float* Q2, const float* q2, float* out, void* stream);
+
 /* With the tensor cores allowed (fno_set_tensor_cores(1), the default), fno_combine runs
  * on them (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory)
  * when in and out are bf16, pre is NULL, m_trans = 0, Ci = 32 and Co is 32 or
- * 64 -- the BF16 inference path of the Fourier layers and the first
- * projection; the weights, the table and the spectral coefficients are rounded
+ * 64 -- the BF16 inference path of the Fourier layers (and fno_project under
+ * the conditions stated there); the weights, the table and the spectral coefficients are rounded
  * to BF16 on their way into shared memory.  fno_set_tensor_cores(0) keeps the
  * CUDA-core kernel everywhere.  fno_tensor_core_status synchronises the device,
  * returns WAVE_ERR_TIMEOUT if a tensor-core launch since the last call gave up

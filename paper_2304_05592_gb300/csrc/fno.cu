@@ -274,11 +274,13 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
         const float* mr = sM + o * CIMAX;
 #pragma unroll
         for (int i = 0; i < CIMAX; ++i) acc = fmaf(mr[i], v[i], acc);
-        const float* tr = sT + o * 32;
+        if (T) {  // uniform over the grid
+            const float* tr = sT + o * 32;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            acc = fmaf(tr[2 * k], tc[k], acc);
-            acc = fmaf(-tr[2 * k + 1], ts[k], acc);
+            for (int k = 0; k < 16; ++k) {
+                acc = fmaf(tr[2 * k], tc[k], acc);
+                acc = fmaf(-tr[2 * k + 1], ts[k], acc);
+            }
         }
         const size_t oi = ((size_t)b * co + o) * npix + pix;
         if (pre) pre[oi] = acc;
@@ -384,27 +386,33 @@ constexpr int kTcTs = 36;  // floats per row of the raw T buffer (32 + 4 of padd
 // cleared by fno_tensor_core_status.
 __device__ int g_tc_err;
 
-// dynamic shared memory of k_combine_tc<CO>, in bytes (all pieces 16-byte aligned)
-__host__ __device__ constexpr int tc_smem_bytes(int co)
+// dynamic shared memory of k_combine_tc<co, proj>, in bytes (all pieces 16-byte
+// aligned; the projection needs only the activations and the weights)
+__host__ __device__ constexpr int tc_smem_bytes(int co, bool proj)
 {
-    return 2 * 8192 /*A1 x2*/ + 8192 /*A2*/ + co * 64 /*B1*/ + 2 * co * 64 /*B2 x2*/ + 2 * co * kTcTs * 4 /*raw T x2*/ +
-           co * (128 + 8) * 2 /*output transpose*/;
+    return proj ? 2 * 8192 + co * 64
+                : 2 * 8192 /*A1 x2*/ + co * 64 /*B1*/ + 8192 /*A2*/ + 2 * co * 64 /*B2 x2*/ +
+                      2 * co * kTcTs * 4 /*raw T x2*/ + co * (128 + 8) * 2 /*output transpose*/;
 }
 
-template <int CO>
+// PROJ: the projection head instead of a BF16 output -- out (float, one channel)
+// = q2 + sum_o Q2[o] GELU(D[p][o] + bias[o]); T must be NULL.
+template <int CO, bool PROJ>
 __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int rw, const __nv_bfloat16* __restrict__ in,
                                                     const float* __restrict__ M, const float* __restrict__ bias,
                                                     const float* __restrict__ T, const float* __restrict__ tab,
-                                                    int act, __nv_bfloat16* __restrict__ out)
+                                                    int act, const float* __restrict__ Q2, const float* __restrict__ q2,
+                                                    void* __restrict__ out_)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* const sA1 = smem;               // [2][8192]
-    unsigned char* const sA2 = smem + 2 * 8192;    // [8192]
-    unsigned char* const sB1 = sA2 + 8192;         // [CO * 64]
-    unsigned char* const sB2 = sB1 + CO * 64;      // [2][CO * 64]
+    unsigned char* const sB1 = smem + 2 * 8192;    // [CO * 64]
+    unsigned char* const sA2 = sB1 + CO * 64;      // [8192]
+    unsigned char* const sB2 = sA2 + 8192;         // [2][CO * 64]
     float* const sT = reinterpret_cast<float*>(sB2 + 2 * CO * 64);  // [2][CO][kTcTs]
     __nv_bfloat16(*const sOut)[128 + 8] = reinterpret_cast<__nv_bfloat16(*)[128 + 8]>(sT + 2 * CO * kTcTs);
-    __shared__ float sbias[CO];
+    __nv_bfloat16* const out = static_cast<__nv_bfloat16*>(out_);
+    __shared__ float sbias[CO], sq2[CO + 1];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -519,6 +527,8 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
             *reinterpret_cast<uint4*>(sA2 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
     }
     for (int o = tid; o < CO; o += 128) sbias[o] = bias ? bias[o] : 0.0f;
+    if (PROJ)
+        for (int o = tid; o <= CO; o += 128) sq2[o] = o < CO ? Q2[o] : (q2 ? q2[0] : 0.0f);
     if (nrows > 1) cp_async_wait_prev();
     else cp_async_wait_all();
     __syncthreads();  // row 0's raw T visible to every thread
@@ -535,8 +545,10 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
         const int cur = it & 1, nxt = cur ^ 1;
         if (it + 1 < nrows) {
             cp_async_wait_all();  // this thread's copies of row it+1
-            __syncthreads();
-            convert(nxt);
+            if (spectral) {
+                __syncthreads();  // every thread's raw T before the conversion
+                convert(nxt);
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -547,6 +559,22 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (it + 2 < nrows) prefetch(it + 2, cur);  // into the buffers row it's MMAs have finished reading
+        if (PROJ) {
+            if (ok) {
+                const uint32_t ta = tm + (uint32_t)(cur * CO) + ((uint32_t)(warp * 32) << 16);
+                const int x = x0 + warp * 32 + lane;  // accumulator lane = pixel of the tile
+                float y = sq2[CO];
+#pragma unroll
+                for (int half = 0; half < CO / 32; ++half) {
+                    float v[32];
+                    tmem_ld32(ta + half * 32, v);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) y = fmaf(sq2[half * 32 + c], gelu(v[c] + sbias[half * 32 + c]), y);
+                }
+                if (x < Nx) static_cast<float*>(out_)[(size_t)b * npix + (size_t)(z0 + it) * Nx + x] = y;
+            }
+            continue;  // the next row's barrier orders this accumulator read before its reuse
+        }
         if (ok) {
             const uint32_t ta = tm + (uint32_t)(cur * CO) + ((uint32_t)(warp * 32) << 16);
             const int p = warp * 32 + lane;  // accumulator lane = pixel of the tile
@@ -699,6 +727,40 @@ __global__ void __launch_bounds__(128) k_dft_x_tc(long long rows, int Nx, int n2
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tm) : "memory");
+}
+
+// --- projection head on the CUDA cores ------------------------------------------------
+// out[b][p] = q2 + sum_h Q2[h] GELU(q1[h] + sum_i Q1[h][i] in[b][i][p]): the
+// two pointwise layers of the head in one pass, the hidden channels kept in
+// registers.  One thread per pixel; the weights in shared memory.
+template <int CIMAX, typename Tin>
+__global__ void __launch_bounds__(256) k_project(int ci, int H, long long npix, const Tin* __restrict__ in,
+                                                 const float* __restrict__ Q1, const float* __restrict__ q1,
+                                                 const float* __restrict__ Q2, const float* __restrict__ q2,
+                                                 float* __restrict__ out)
+{
+    extern __shared__ float w[];  // Q1 [H][ci], then q1 [H] and Q2 [H]
+    const int tid = threadIdx.x, b = blockIdx.y;
+    for (int e = tid; e < H * ci; e += 256) w[e] = Q1[e];
+    for (int h = tid; h < H; h += 256) {
+        w[H * ci + h] = q1 ? q1[h] : 0.0f;
+        w[H * ci + H + h] = Q2[h];
+    }
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * 256 + tid;
+    if (p >= npix) return;
+    float x[CIMAX];
+#pragma unroll
+    for (int i = 0; i < CIMAX; ++i) x[i] = i < ci ? ldf(in, ((size_t)b * ci + i) * npix + p) : 0.0f;
+    float y = q2 ? q2[0] : 0.0f;
+    for (int h = 0; h < H; ++h) {
+        float acc = w[H * ci + h];
+#pragma unroll
+        for (int i = 0; i < CIMAX; ++i)
+            if (i < ci) acc = fmaf(w[h * ci + i], x[i], acc);
+        y = fmaf(w[H * ci + H + h], gelu(acc), y);
+    }
+    out[(size_t)b * npix + p] = y;
 }
 
 // --- weight gradients ---------------------------------------------------------------
@@ -870,9 +932,9 @@ void combine_launch(int B, int ci, int co, int Nz, int Nx, int mx, const void* i
                                                          T, tab, act, pre, static_cast<Tout*>(out));
 }
 
-// Resident CTAs of k_combine_tc<CO> on the whole device (per device, found
+// Resident CTAs of k_combine_tc<CO, PROJ> on the whole device (per device, found
 // once), from the kernel's registers and shared memory against the SM's limits.
-template <int CO>
+template <int CO, bool PROJ>
 int tc_slots()
 {
     static int slots[64] = {0};
@@ -882,18 +944,19 @@ int tc_slots()
         cudaFuncAttributes fa;
         int nsm = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0, thr_sm = 0;
         // all of the unified L1 as shared memory
-        if (cudaFuncSetAttribute(k_combine_tc<CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(CO)) !=
+        const int smem_dyn = tc_smem_bytes(CO, PROJ);
+        if (cudaFuncSetAttribute(k_combine_tc<CO, PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dyn) !=
                 cudaSuccess ||
-            cudaFuncSetAttribute(k_combine_tc<CO>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_combine_tc<CO, PROJ>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, k_combine_tc<CO>) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, k_combine_tc<CO, PROJ>) != cudaSuccess ||
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
             return 0;
-        const int smem_cta = tc_smem_bytes(CO) + (int)fa.sharedSizeBytes + smem_rsv;
+        const int smem_cta = smem_dyn + (int)fa.sharedSizeBytes + smem_rsv;
         const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
         int occ = std::min(smem_sm / smem_cta, thr_sm / 128);
         if (regs_warp > 0) occ = std::min(occ, regs_sm / (4 * regs_warp));
@@ -907,18 +970,19 @@ int tc_slots()
 
 // One wave: rows per CTA so that the (x tiles) x (row chunks) x B grid fills
 // the resident slots once.
-template <int CO>
+template <int CO, bool PROJ>
 wave_status_t combine_tc_launch(int B, int Nz, int Nx, int mx, const void* in, const float* M, const float* bias,
-                                const float* T, const float* tab, int act, void* out, cudaStream_t s)
+                                const float* T, const float* tab, int act, const float* Q2, const float* q2, void* out,
+                                cudaStream_t s)
 {
-    const int slots = tc_slots<CO>();
+    const int slots = tc_slots<CO, PROJ>();
     if (slots <= 0) return WAVE_ERR_CUDA;
     const long long xt = (Nx + 127) / 128, tiles = xt * Nz * (long long)B;
     int rw = (int)std::min<long long>(Nz, std::max<long long>(1, (tiles + slots - 1) / slots));
     while (rw < Nz && xt * ((Nz + rw - 1) / rw) * B > slots) ++rw;  // rounding must not spill into a second wave
     dim3 grid((unsigned)xt, (unsigned)((Nz + rw - 1) / rw), B);
-    k_combine_tc<CO><<<grid, 128, tc_smem_bytes(CO), s>>>(Nz, Nx, mx, rw, static_cast<const __nv_bfloat16*>(in), M, bias,
-                                                           T, tab, act, static_cast<__nv_bfloat16*>(out));
+    k_combine_tc<CO, PROJ><<<grid, 128, tc_smem_bytes(CO, PROJ), s>>>(
+        Nz, Nx, mx, rw, static_cast<const __nv_bfloat16*>(in), M, bias, T, tab, act, Q2, q2, out);
     return launched();
 }
 
@@ -1036,8 +1100,8 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
     const int mxe = T ? mx : 1;
     if (g_tensor_cores && in_bf16 && out_bf16 && !pre && !m_trans && Ci == kTcCi && (Co == 32 || Co == 64)) {
         if (Co == 32)
-            return combine_tc_launch<32>(B, Nz, Nx, mxe, in, M, bias, T, table, act, out, s);
-        return combine_tc_launch<64>(B, Nz, Nx, mxe, in, M, bias, T, table, act, out, s);
+            return combine_tc_launch<32, false>(B, Nz, Nx, mxe, in, M, bias, T, table, act, nullptr, nullptr, out, s);
+        return combine_tc_launch<64, false>(B, Nz, Nx, mxe, in, M, bias, T, table, act, nullptr, nullptr, out, s);
     }
     if (in_bf16 && out_bf16)
         combine_dispatch<__nv_bfloat16, __nv_bfloat16>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre,
@@ -1048,6 +1112,42 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
         combine_dispatch<float, __nv_bfloat16>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre, out, s);
     else
         combine_dispatch<float, float>(B, Ci, Co, Nz, Nx, mxe, in, M, m_trans, bias, T, table, act, pre, out, s);
+    return launched();
+}
+
+wave_status_t fno_project(int B, int Ci, int H, int Nz, int Nx, const void* in, int in_bf16, const float* Q1,
+                          const float* q1, const float* Q2, const float* q2, float* out, void* stream)
+{
+    if (B < 0 || Ci < 1 || Ci > 64 || H < 1 || H > 64 || Nz < 1 || Nx < 1 || !in || !Q1 || !Q2 || !out)
+        return WAVE_ERR_ARG;
+    if (B == 0) return WAVE_OK;
+    if (B > 65535 || Nz > 65535) return WAVE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g_tensor_cores && in_bf16 && Ci == kTcCi && (H == 32 || H == 64)) {
+        if (H == 32)
+            return combine_tc_launch<32, true>(B, Nz, Nx, 1, in, Q1, q1, nullptr, nullptr, FNO_ACT_GELU, Q2, q2, out, s);
+        return combine_tc_launch<64, true>(B, Nz, Nx, 1, in, Q1, q1, nullptr, nullptr, FNO_ACT_GELU, Q2, q2, out, s);
+    }
+    const long long npix = (long long)Nz * Nx, nblk = (npix + 255) / 256;
+    if (nblk > 0x7fffffffLL) return WAVE_ERR_ARG;
+    const dim3 grid((unsigned)nblk, B);
+    const size_t smem = (size_t)(H * Ci + 2 * H) * sizeof(float);
+#define WAVE_PROJECT(CIMAX)                                                                                        \
+    do {                                                                                                           \
+        if (in_bf16)                                                                                               \
+            k_project<CIMAX, __nv_bfloat16><<<grid, 256, smem, s>>>(Ci, H, npix,                                   \
+                                                                     static_cast<const __nv_bfloat16*>(in), Q1, q1, \
+                                                                     Q2, q2, out);                                 \
+        else                                                                                                       \
+            k_project<CIMAX, float><<<grid, 256, smem, s>>>(Ci, H, npix, static_cast<const float*>(in), Q1, q1, Q2, \
+                                                             q2, out);                                             \
+    } while (0)
+    if (Ci <= 4) WAVE_PROJECT(4);
+    else if (Ci <= 8) WAVE_PROJECT(8);
+    else if (Ci <= 16) WAVE_PROJECT(16);
+    else if (Ci <= 32) WAVE_PROJECT(32);
+    else WAVE_PROJECT(64);
+#undef WAVE_PROJECT
     return launched();
 }
 

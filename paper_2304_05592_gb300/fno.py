@@ -42,6 +42,7 @@ def _lib():
             "fno_mix": [I, I, I, I, P, P, P, P],
             "fno_mix_backward": [I, I, I, I, P, P, P, P, P, P],
             "fno_combine": [I, I, I, I, I, I, P, I, P, I, P, P, P, I, P, P, I, P],
+            "fno_project": [I, I, I, I, I, P, I, P, P, P, P, P, P],
             "fno_wgrad": [I, I, I, L, P, P, P, P, P, P],
             "fno_gelu_backward": [L, P, P, P, P],
             "fno_mse": [L, P, P, P, P, P, P],
@@ -133,6 +134,17 @@ def fno_combine(inp, M, Co, m_trans=False, bias=None, T=None, table=None, mx=1, 
         out = torch.empty((B, Co, Nz, Nx), dtype=out_dtype, device=inp.device)
     _call("fno_combine", B, Ci, Co, Nz, Nx, mx, _p(inp), int(inp.dtype == torch.bfloat16), _p(M), int(m_trans),
           _p(bias), _p(T), _p(table), act, _p(pre), _p(out), int(out.dtype == torch.bfloat16), _s(stream))
+    return out
+
+
+def fno_project(inp, Q1, q1, Q2, q2, out=None, stream=None):
+    """out = q2 + Q2 GELU(Q1 inp + q1) per pixel, the hidden channels kept on chip."""
+    B, Ci, Nz, Nx = inp.shape
+    H = Q1.shape[0]
+    if out is None:
+        out = torch.empty((B, 1, Nz, Nx), dtype=torch.float32, device=inp.device)
+    _call("fno_project", B, Ci, H, Nz, Nx, _p(inp), int(inp.dtype == torch.bfloat16), _p(Q1), _p(q1), _p(Q2), _p(q2),
+          _p(out), _s(stream))
     return out
 
 
@@ -285,10 +297,14 @@ class FNO2d:
             if train:
                 layers.append((v, X, pre if not last else vn))
             v = vn
-        hpre = torch.empty((B, cfg.hidden, Nz, Nx), dtype=torch.float32, device=x.device) if train else None
+        if not train:
+            self._cache = None
+            return fno_project(v, self.view("Q1"), self.view("q1"), self.view("Q2"),
+                               self.view("q2"))
+        hpre = torch.empty((B, cfg.hidden, Nz, Nx), dtype=torch.float32, device=x.device)
         h = fno_combine(v, self.view("Q1"), cfg.hidden, bias=self.view("q1"), act=ACT_GELU, pre=hpre, out_dtype=adt)
         out = fno_combine(h, self.view("Q2"), 1, bias=self.view("q2"))
-        self._cache = dict(x=x, layers=layers, v=v, hpre=hpre, h=h) if train else None
+        self._cache = dict(x=x, layers=layers, v=v, hpre=hpre, h=h)
         return out
 
     def backward(self, dout: torch.Tensor):

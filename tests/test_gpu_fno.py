@@ -137,6 +137,8 @@ def test_network_forward_backward_match_oracle(cfg, Nz, Nx, B):
     net.forward(dev(x), train=True)
     net.backward(dout)
     assert torch.equal(first, net.grads)
+    # FP32 inference (fused projection head) agrees like the training forward
+    assert rel(net.forward(dev(x), train=False).cpu().numpy(), out_ref) < TOL
     # BF16 activations (inference): error stated, bounded by 1e-2
     out16 = net.forward(dev(x), train=False, bf16=True)
     e16 = rel(out16.cpu().numpy(), out_ref)
@@ -233,3 +235,32 @@ def test_tensor_core_x_transform_matches_reference(shape):
     ref = vf @ tab
     assert rel(out_tc.reshape(ref.shape), ref) < 1e-2
     assert rel(out_cc.reshape(ref.shape), ref) < 1e-5
+
+
+@pytest.mark.parametrize("dtype,Ci,H,Nz,Nx,tc", [
+    (torch.bfloat16, 32, 64, 301, 264, True),  # tensor cores, cp.async staging, rows per CTA > 1, ragged tile
+    (torch.bfloat16, 32, 32, 12, 300, True),   # tensor cores, element-wise staging
+    (torch.bfloat16, 32, 64, 40, 512, False),  # CUDA cores on BF16 input
+    (torch.float32, 32, 64, 37, 70, False),
+    (torch.float32, 5, 7, 9, 33, False)])
+def test_fused_projection_matches_two_layers_and_reference(dtype, Ci, H, Nz, Nx, tc):
+    """fno_project (both head layers in one pass) against two fno_combine calls
+    and an FP64 reference from the same input values."""
+    B = 2
+    x = torch.from_numpy(RNG.standard_normal((B, Ci, Nz, Nx)).astype(np.float32)).cuda().to(dtype)
+    Q1, q1 = RNG.standard_normal((H, Ci)) / np.sqrt(Ci), RNG.standard_normal(H)
+    Q2, q2 = RNG.standard_normal((1, H)) / np.sqrt(H), RNG.standard_normal(1)
+    try:
+        fno.fno_set_tensor_cores(tc)
+        out = fno.fno_project(x, dev(Q1), dev(q1), dev(Q2), dev(q2)).cpu().numpy()
+        assert fno.fno_tensor_core_status() == 0
+    finally:
+        fno.fno_set_tensor_cores(True)
+    h = fno.fno_combine(x, dev(Q1), H, bias=dev(q1), act=fno.ACT_GELU)  # float hidden layer, CUDA cores
+    two = fno.fno_combine(h, dev(Q2), 1, bias=dev(q2)).cpu().numpy()
+    xf = x.float().cpu().numpy().astype(np.float64)
+    ref = ofno.pointwise(Q2, q2, ofno.gelu(ofno.pointwise(Q1, q1, xf)))
+    assert out.shape == (B, 1, Nz, Nx)
+    assert rel(two, ref) < 1e-5
+    # tensor cores: Q1 rounded to BF16 on its way in; otherwise float arithmetic throughout
+    assert rel(out, ref) < (1e-2 if tc else 1e-5), rel(out, ref)
