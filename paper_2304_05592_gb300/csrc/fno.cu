@@ -290,35 +290,40 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
 
 // --- the same channel mix on the 5th-generation tensor cores (BF16 inference) -----------
 // One CTA (4 warps) computes 128-pixel pieces of rw consecutive rows (b, z) for
-// all co outputs, one row at a time, as D[128 x co] = A1 B1^T + A2 B2^T with
-// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory):
+// all co outputs, one row at a time, as
+//   D[128 x co] = A1 B1^T + A2 B2^T + A3 B3^T
+// with tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory):
 //   A1[p][i] = in[b][i][z][x0+p]        B1[o][i] = M[o][i]
 //   A2[p][k] = table[x0+p][k]           B2[o][k] = (T re, -T im)[b][o][z][k]
-// (k = 2 kx + {0, 1}), so that A2 B2^T is the x part of the spectral inverse.
+//   A3[p][k] = (1, 1, 0, ...)           B3[o][k] = (hi, lo, 0, ...) with
+// (k = 2 kx + {0, 1} in A2, B2) so that A2 B2^T is the x part of the spectral
+// inverse and A3 B3^T adds the bias, split into two BF16 parts hi + lo (bias
+// to about 16 significant bits) so that the epilogue reads finished sums.
 // Operands sit in shared memory without swizzle, in core matrices of 8 rows x
-// 16 bytes: B1, A2 and B2 K-major (element (r, k) at (r/8)*512 + (k/8)*128 +
-// (r%8)*16 + (k%8)*2 bytes), A1 pixel-major (element (p, i) at (p/8)*512 +
-// (i/8)*128 + (i%8)*16 + (p%8)*2), which is how the activations lie in memory:
-// every 16-byte piece of 8 pixels of one channel is copied as it is
-// (cp.async) and the MMA reads A1 transposed.  In both layouts the
-// descriptor's leading offset (128 B) steps along K and its stride offset
-// (512 B) along rows.  Pipeline, for row it: row it+1's activations and T
-// arrived during row it-1; T is converted to BF16 and row it+1's MMAs go to
-// the second accumulator; row it's MMAs are waited for, row it+2's copies go
-// into the buffers row it has finished with, and row it's accumulator is read
-// (tcgen05.ld), biased, passed through GELU and stored BF16 through a shared
-// transpose so that each warp writes whole rows.  Requires ci = 32, co in
-// {32, 64}, mx <= 16.
+// 16 bytes: B1, A2, B2 K-major (element (r, k) at (r/8)*512 + (k/8)*128 +
+// (r%8)*16 + (k%8)*2 bytes), A3, B3 K-major with 256 bytes between row
+// groups, A1 pixel-major (element (p, i) at (p/8)*512 + (i/8)*128 + (i%8)*16 +
+// (p%8)*2), which is how the activations lie in memory: every 16-byte piece of
+// 8 pixels of one channel is copied as it is (cp.async) and the MMA reads A1
+// transposed.  In all layouts the descriptor's leading offset (128 B) steps
+// along K and its stride offset along rows.  Pipeline, for row it: row it+1's
+// activations and T arrived during row it-1; T is converted to BF16 and row
+// it+1's MMAs go to the second accumulator; row it's MMAs are waited for, row
+// it+2's copies go into the buffers row it has finished with, and row it's
+// accumulator is read (tcgen05.ld), passed through GELU and stored BF16 straight
+// from registers: lane = pixel, so a warp writes 64 contiguous bytes of each
+// output channel.  Requires ci = 32, co in {32, 64}, mx <= 16.
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+__device__ __forceinline__ uint64_t umma_desc_sbo(uint32_t saddr, uint32_t sbo)
 {
-    // start address, leading (K) offset 128 B, stride (row-group) offset 512 B,
+    // start address, leading (K) offset 128 B, stride (row-group) offset sbo,
     // descriptor version 1, no swizzle
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
            ((uint64_t)1 << 46);
 }
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) { return umma_desc_sbo(saddr, 512); }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
@@ -379,24 +384,54 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2 with erf from Abramowitz and
+// Stegun, Handbook of Mathematical Functions, formula 7.1.26 (after Hastings):
+// erf(a) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-a^2), t = 1 / (1 + p a),
+// a >= 0, |error| <= 1.5e-7.  The exponential and the reciprocal are the
+// hardware approximations (ex2.approx, rcp.approx; relative errors near 2^-22),
+// which keeps this at about 15 instructions.  Used by the BF16 tensor-core
+// epilogues, whose outputs carry 8 significant bits.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu_as(float x)
+{
+    const float a = fabsf(x) * 0.70710678118654752f;
+    const float t = rcp_approx(fmaf(0.3275911f, a, 1.0f));
+    float q = fmaf(t, 1.061405429f, -1.453152027f);
+    q = fmaf(t, q, 1.421413741f);
+    q = fmaf(t, q, -0.284496736f);
+    q = fmaf(t, q, 0.254829592f);
+    // half of erfc(a) = q t exp(-a^2) / 2, exp(-a^2) = 2^(-a^2 log2 e), a^2 = x^2 / 2
+    const float h = 0.5f * q * t * ex2_approx(-0.72134752044448170f * x * x);
+    return x * (x >= 0.0f ? 1.0f - h : h);
+}
+
 constexpr int kTcCi = 32;
-constexpr int kTcTs = 36;  // floats per row of the raw T buffer (32 + 4 of padding against bank conflicts)
 
 // Set by the tensor-core kernels if a wait for their MMAs gives up; read and
 // cleared by fno_tensor_core_status.
 __device__ int g_tc_err;
 
 // dynamic shared memory of k_combine_tc<co, proj>, in bytes (all pieces 16-byte
-// aligned; the projection needs only the activations and the weights)
+// aligned; the projection needs no table and no spectral term)
 __host__ __device__ constexpr int tc_smem_bytes(int co, bool proj)
 {
-    return proj ? 2 * 8192 + co * 64
-                : 2 * 8192 /*A1 x2*/ + co * 64 /*B1*/ + 8192 /*A2*/ + 2 * co * 64 /*B2 x2*/ +
-                      2 * co * kTcTs * 4 /*raw T x2*/ + co * (128 + 8) * 2 /*output transpose*/;
+    return 2 * 8192 /*A1 x2*/ + co * 64 /*B1*/ + 4096 /*A3*/ + co * 32 /*B3*/ +
+           (proj ? 0 : 8192 /*A2*/ + 2 * co * 64 /*B2 x2*/ + 2 * co * 32 * 4 /*raw T x2*/);
 }
 
 // PROJ: the projection head instead of a BF16 output -- out (float, one channel)
-// = q2 + sum_o Q2[o] GELU(D[p][o] + bias[o]); T must be NULL.
+// = q2 + sum_o Q2[o] GELU(D[p][o]); T must be NULL.
 template <int CO, bool PROJ>
 __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int rw, const __nv_bfloat16* __restrict__ in,
                                                     const float* __restrict__ M, const float* __restrict__ bias,
@@ -404,15 +439,15 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
                                                     int act, const float* __restrict__ Q2, const float* __restrict__ q2,
                                                     void* __restrict__ out_)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* const sA1 = smem;               // [2][8192]
     unsigned char* const sB1 = smem + 2 * 8192;    // [CO * 64]
-    unsigned char* const sA2 = sB1 + CO * 64;      // [8192]
-    unsigned char* const sB2 = sA2 + 8192;         // [2][CO * 64]
-    float* const sT = reinterpret_cast<float*>(sB2 + 2 * CO * 64);  // [2][CO][kTcTs]
-    __nv_bfloat16(*const sOut)[128 + 8] = reinterpret_cast<__nv_bfloat16(*)[128 + 8]>(sT + 2 * CO * kTcTs);
-    __nv_bfloat16* const out = static_cast<__nv_bfloat16*>(out_);
-    __shared__ float sbias[CO], sq2[CO + 1];
+    unsigned char* const sA3 = sB1 + CO * 64;      // [4096]
+    unsigned char* const sB3 = sA3 + 4096;         // [CO * 32]
+    unsigned char* const sA2 = sB3 + CO * 32;      // [8192]            (not PROJ)
+    unsigned char* const sB2 = sA2 + 8192;         // [2][CO * 64]      (not PROJ)
+    float* const sT = reinterpret_cast<float*>(sB2 + 2 * CO * 64);  // [2][CO][32] (not PROJ)
+    __shared__ float sq2[CO + 1];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -420,7 +455,7 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
     const int z0 = blockIdx.y * rw, nrows = min(rw, Nz - z0);
     const size_t npix = (size_t)Nz * Nx;
     const int n2 = 2 * mx;
-    const bool spectral = T != nullptr;
+    const bool spectral = !PROJ && T != nullptr;
     const bool vecA = (Nx & 7) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
     const bool vecT = (n2 & 3) == 0 && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
     if (nrows <= 0) return;  // uniform over the CTA
@@ -460,16 +495,16 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
             }
         }
         if (spectral) {
-            float* t = sT + slot * CO * kTcTs;
+            float* t = sT + slot * CO * 32;
             if (vecT) {
                 for (int e = tid; e < CO * 8; e += 128) {
                     const int o = e >> 3, j = e & 7;
-                    if (4 * j < n2) cp_async16(su32(t + o * kTcTs + 4 * j), T + (((size_t)b * CO + o) * Nz + z) * n2 + 4 * j, 16);
+                    if (4 * j < n2) cp_async16(su32(t + o * 32 + 4 * j), T + (((size_t)b * CO + o) * Nz + z) * n2 + 4 * j, 16);
                 }
             } else {
                 for (int e = tid; e < CO * 32; e += 128) {
                     const int o = e >> 5, k = e & 31;
-                    if (k < n2) t[o * kTcTs + k] = T[(((size_t)b * CO + o) * Nz + z) * n2 + k];
+                    if (k < n2) t[o * 32 + k] = T[(((size_t)b * CO + o) * Nz + z) * n2 + k];
                 }
             }
         }
@@ -477,16 +512,15 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
     };
     // raw T of buffers `slot` -> B2 (BF16, K-major, odd entries negated)
     auto convert = [&](int slot) {
-        if (!spectral) return;
-        const float* t = sT + slot * CO * kTcTs;
+        const float* t = sT + slot * CO * 32;
         unsigned char* bb = sB2 + slot * CO * 64;
         for (int e = tid; e < CO * 4; e += 128) {
-            const int o = e % CO, kg = e / CO;
+            const int o = e >> 2, kg = e & 3;
             float g[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int k = 8 * kg + j;
-                const float v = k < n2 ? t[o * kTcTs + k] : 0.0f;
+                const float v = k < n2 ? t[o * 32 + k] : 0.0f;
                 g[j] = (k & 1) ? -v : v;
             }
             *reinterpret_cast<uint4*>(bb + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
@@ -498,6 +532,7 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
 #pragma unroll
         for (int j = 0; j < kTcCi / 16; ++j)
             umma_bf16(tm, umma_desc(su32(sA1 + slot * 8192) + j * 256), umma_desc(su32(sB1) + j * 256), idesc_a1, j > 0);
+        umma_bf16(tm, umma_desc_sbo(su32(sA3), 256), umma_desc_sbo(su32(sB3), 256), idesc_k, 1u);
         if (spectral) {
 #pragma unroll
             for (int j = 0; j < 2; ++j)
@@ -509,13 +544,27 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
 
     prefetch(0, 0);
     if (nrows > 1) prefetch(1, 1);
-    // set up once per CTA while the first rows are in flight: weights, table, bias
+    // set up once per CTA while the first rows are in flight: weights, bias, table
     for (int e = tid; e < CO * 4; e += 128) {
         const int o = e >> 2, kg = e & 3;
         float g[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) g[j] = M[(size_t)o * kTcCi + 8 * kg + j];
         *reinterpret_cast<uint4*>(sB1 + (o >> 3) * 512 + kg * 128 + (o & 7) * 16) = pack8_bf16(g);
+    }
+    {
+        // A3: ones in k = 0, 1 of every pixel row; B3: the bias as hi + lo in k = 0, 1
+        float g[8] = {1.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const float z8[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        *reinterpret_cast<uint4*>(sA3 + (tid >> 3) * 256 + (tid & 7) * 16) = pack8_bf16(g);
+        *reinterpret_cast<uint4*>(sA3 + (tid >> 3) * 256 + 128 + (tid & 7) * 16) = pack8_bf16(z8);
+        if (tid < CO) {
+            const float bo = bias ? bias[tid] : 0.0f;
+            g[0] = __bfloat162float(__float2bfloat16_rn(bo));
+            g[1] = bo - g[0];
+            *reinterpret_cast<uint4*>(sB3 + (tid >> 3) * 256 + (tid & 7) * 16) = pack8_bf16(g);
+            *reinterpret_cast<uint4*>(sB3 + (tid >> 3) * 256 + 128 + (tid & 7) * 16) = pack8_bf16(z8);
+        }
     }
     if (spectral) {
         const int x = x0 + tid;
@@ -526,13 +575,12 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
         for (int kg = 0; kg < 4; ++kg)
             *reinterpret_cast<uint4*>(sA2 + (tid >> 3) * 512 + kg * 128 + (tid & 7) * 16) = pack8_bf16(f + 8 * kg);
     }
-    for (int o = tid; o < CO; o += 128) sbias[o] = bias ? bias[o] : 0.0f;
     if (PROJ)
         for (int o = tid; o <= CO; o += 128) sq2[o] = o < CO ? Q2[o] : (q2 ? q2[0] : 0.0f);
     if (nrows > 1) cp_async_wait_prev();
     else cp_async_wait_all();
     __syncthreads();  // row 0's raw T visible to every thread
-    convert(0);
+    if (spectral) convert(0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -541,6 +589,7 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
     if (tid == 0) issue(0, tm);
 
     bool ok = true;
+    const int x = x0 + warp * 32 + lane;  // accumulator lane = pixel of the tile
     for (int it = 0; it < nrows; ++it) {
         const int cur = it & 1, nxt = cur ^ 1;
         if (it + 1 < nrows) {
@@ -552,58 +601,33 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // row it+1's operands complete; the previous row's stores have read sOut
+        __syncthreads();  // row it+1's operands complete; row it-1's accumulator has been read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (it + 1 < nrows && tid == 0) issue(nxt, tm + (uint32_t)(nxt * CO));
         ok = mbar_wait_parity(&bar[cur], (uint32_t)(it >> 1) & 1u) && ok;  // row it's MMAs are done
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (it + 2 < nrows) prefetch(it + 2, cur);  // into the buffers row it's MMAs have finished reading
-        if (PROJ) {
-            if (ok) {
-                const uint32_t ta = tm + (uint32_t)(cur * CO) + ((uint32_t)(warp * 32) << 16);
-                const int x = x0 + warp * 32 + lane;  // accumulator lane = pixel of the tile
-                float y = sq2[CO];
+        if (!ok) continue;
+        const uint32_t ta = tm + (uint32_t)(cur * CO) + ((uint32_t)(warp * 32) << 16);
+        const size_t row = (size_t)b * (PROJ ? 1 : CO) * npix + (size_t)(z0 + it) * Nx + x;
+        float y = PROJ ? sq2[CO] : 0.0f;
 #pragma unroll
-                for (int half = 0; half < CO / 32; ++half) {
-                    float v[32];
-                    tmem_ld32(ta + half * 32, v);
+        for (int half = 0; half < CO / 32; ++half) {
+            float v[32];
+            tmem_ld32(ta + half * 32, v);
+            if (PROJ) {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) y = fmaf(sq2[half * 32 + c], gelu(v[c] + sbias[half * 32 + c]), y);
-                }
-                if (x < Nx) static_cast<float*>(out_)[(size_t)b * npix + (size_t)(z0 + it) * Nx + x] = y;
-            }
-            continue;  // the next row's barrier orders this accumulator read before its reuse
-        }
-        if (ok) {
-            const uint32_t ta = tm + (uint32_t)(cur * CO) + ((uint32_t)(warp * 32) << 16);
-            const int p = warp * 32 + lane;  // accumulator lane = pixel of the tile
+                for (int c = 0; c < 32; ++c) y = fmaf(sq2[half * 32 + c], gelu_as(v[c]), y);
+            } else if (x < Nx) {
+                __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(out_) + row + (size_t)(half * 32) * npix;
 #pragma unroll
-            for (int half = 0; half < CO / 32; ++half) {
-                float v[32];
-                tmem_ld32(ta + half * 32, v);
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const float r = v[c] + sbias[half * 32 + c];
-                    sOut[half * 32 + c][p] = __float2bfloat16_rn(act == FNO_ACT_GELU ? gelu(r) : r);
-                }
+                for (int c = 0; c < 32; ++c)
+                    dst[(size_t)c * npix] = __float2bfloat16_rn(act == FNO_ACT_GELU ? gelu_as(v[c]) : v[c]);
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // sOut complete; row it's accumulator has been read
-        if (ok) {
-            // coalesced stores: a warp writes 128 pixels (4 per lane) of one output channel
-            const int z = z0 + it, xs = x0 + 4 * lane;
-            for (int o = warp; o < CO; o += 4) {
-                __nv_bfloat16* dst = out + ((size_t)b * CO + o) * npix + (size_t)z * Nx;
-                if ((Nx & 3) == 0 && xs + 3 < Nx) {
-                    *reinterpret_cast<uint2*>(dst + xs) = *reinterpret_cast<const uint2*>(&sOut[o][4 * lane]);
-                } else {
-                    for (int q = 0; q < 4; ++q)
-                        if (xs + q < Nx) dst[xs + q] = sOut[o][4 * lane + q];
-                }
-            }
-        }
+        if (PROJ && x < Nx) static_cast<float*>(out_)[row] = y;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");  // ordered before the next row's barrier
     }
     if (!ok && tid == 0) atomicOr(&g_tc_err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -620,11 +644,6 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
 // buffer's mbarrier, which is waited on before the buffer is refilled.
 constexpr int kTcKc = 64;
 
-__device__ __forceinline__ uint64_t umma_desc_sbo(uint32_t saddr, uint32_t sbo)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
-           ((uint64_t)1 << 46);
-}
 
 
 __global__ void __launch_bounds__(128) k_dft_x_tc(long long rows, int Nx, int n2, const __nv_bfloat16* __restrict__ in,

@@ -264,3 +264,9 @@ def test_fused_projection_matches_two_layers_and_reference(dtype, Ci, H, Nz, Nx,
     assert rel(two, ref) < 1e-5
     # tensor cores: Q1 rounded to BF16 on its way in; otherwise float arithmetic throughout
     assert rel(out, ref) < (1e-2 if tc else 1e-5), rel(out, ref)
+    if tc:
+        # with the same BF16 weights the rest is float: FP32 accumulation, the bias
+        # to 16 bits, GELU by Abramowitz-Stegun 7.1.26 (|erf error| <= 1.5e-7)
+        Q1b = torch.from_numpy(Q1).to(torch.bfloat16).double().numpy()
+        refb = ofno.pointwise(Q2, q2, ofno.gelu(ofno.pointwise(Q1b, q1, xf)))
+        assert rel(out, refb) < 5e-5, rel(out, refb)
