@@ -82,13 +82,16 @@ __global__ void __launch_bounds__(256) k_dft_x(long long rows, int Nx, int n2, c
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[q][c] = 0.0f;
     for (int xc = 0; xc < Nx; xc += kDxChunk) {
-        for (int e = tid; e < kDxRows * kDxChunk; e += 256) {
-            const int row = e / kDxChunk, x = e - row * kDxChunk;
+        // unrolled so that eight loads per thread are in flight before their stores
+#pragma unroll 8
+        for (int k = 0; k < kDxRows * kDxChunk / 256; ++k) {
+            const int e = tid + 256 * k, row = e / kDxChunk, x = e - row * kDxChunk;
             const long long gr = r0 + row;
             sv[row][x] = (gr < rows && xc + x < Nx) ? ldf(in, (size_t)gr * Nx + xc + x) : 0.0f;
         }
-        for (int e = tid; e < kDxChunk * 32; e += 256) {
-            const int x = e >> 5, n = e & 31;
+#pragma unroll
+        for (int k = 0; k < kDxChunk * 32 / 256; ++k) {
+            const int e = tid + 256 * k, x = e >> 5, n = e & 31;
             st[x][n] = (xc + x < Nx && n < n2) ? tab[(size_t)(xc + x) * n2 + n] : 0.0f;
         }
         __syncthreads();
@@ -125,64 +128,71 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
-// out[b][a][kx] = sum_z in[b][z][kx] conj(E[z][a]); one CTA per b.
+// out[b][a][kx] = sum_z in[b][z][kx] conj(E[z][a]); CTA per (b, 8 values of a).
+// Thread (h, al, kx): output (a0 + al, kx), half h of every 64-row chunk of z;
+// the two halves are added at the end (always in the same order).
 __global__ void __launch_bounds__(256) k_dft_z(int Nz, int KZ, int mx, const float2* __restrict__ in,
                                                const float2* __restrict__ tz, float2* __restrict__ out)
 {
-    __shared__ float2 si[32][16];
-    __shared__ float2 se[32][64];
-    const int b = blockIdx.x, tid = threadIdx.x;
-    const int nout = KZ * mx;
-    float2 acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-    for (int z0 = 0; z0 < Nz; z0 += 32) {
-        const int zc = min(32, Nz - z0);
-        for (int e = tid; e < 32 * mx; e += 256) {
-            const int zz = e / mx, kx = e - zz * mx;
-            si[zz][kx] = zz < zc ? in[((size_t)b * Nz + z0 + zz) * mx + kx] : make_float2(0.f, 0.f);
+    __shared__ float2 si[64][16];
+    __shared__ float2 se[64][8];
+    __shared__ float2 red[8][16];
+    const int b = blockIdx.x, a0 = blockIdx.y * 8, tid = threadIdx.x;
+    const int kx = tid & 15, al = (tid >> 4) & 7, h = tid >> 7;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int z0 = 0; z0 < Nz; z0 += 64) {
+        const int zc = min(64, Nz - z0);
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int zz = e >> 4, k = e & 15;
+            si[zz][k] = (zz < zc && k < mx) ? in[((size_t)b * Nz + z0 + zz) * mx + k] : make_float2(0.f, 0.f);
         }
-        for (int e = tid; e < 32 * KZ; e += 256) {
-            const int zz = e / KZ, a = e - zz * KZ;
-            se[zz][a] = zz < zc ? tz[(size_t)(z0 + zz) * KZ + a] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int o = tid + 256 * q;
-            if (o >= nout) continue;
-            const int a = o / mx, kx = o - a * mx;
-            for (int zz = 0; zz < zc; ++zz) acc[q] = cadd(acc[q], cmulc(si[zz][kx], se[zz][a]));
+        for (int e = tid; e < 64 * 8; e += 256) {
+            const int zz = e >> 3, a = e & 7;
+            se[zz][a] = (zz < zc && a0 + a < KZ) ? tz[(size_t)(z0 + zz) * KZ + a0 + a] : make_float2(0.f, 0.f);
         }
         __syncthreads();
+#pragma unroll 8
+        for (int zz = 32 * h; zz < 32 * h + 32; ++zz) acc = cadd(acc, cmulc(si[zz][kx], se[zz][al]));
+        __syncthreads();
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int o = tid + 256 * q;
-        if (o < nout) out[(size_t)b * nout + o] = acc[q];
-    }
+    if (h == 1) red[al][kx] = acc;
+    __syncthreads();
+    if (h == 0 && kx < mx && a0 + al < KZ) out[((size_t)b * KZ + a0 + al) * mx + kx] = cadd(acc, red[al][kx]);
 }
 
-// out[b][z][kx] = sum_a in[b][a][kx] E[z][a]; CTA per (b, 32 rows of z).
+// out[b][z][kx] = sum_a in[b][a][kx] E[z][a]; CTA per (b, 64 rows of z).
+// Thread (zr, kx) computes rows zr, zr+16, zr+32, zr+48 of its kx, so that each
+// in[a][kx] read from shared memory feeds four outputs.
 __global__ void __launch_bounds__(256) k_idft_z(int Nz, int KZ, int mx, const float2* __restrict__ in,
                                                 const float2* __restrict__ tz, float2* __restrict__ out)
 {
     __shared__ float2 sx[64][16];
-    __shared__ float2 se[32][64];
-    const int b = blockIdx.x, z0 = blockIdx.y * 32, tid = threadIdx.x;
-    for (int e = tid; e < KZ * mx; e += 256) sx[e / mx][e % mx] = in[(size_t)b * KZ * mx + e];
-    for (int e = tid; e < 32 * KZ; e += 256) {
+    __shared__ float2 se[64][65];
+    const int b = blockIdx.x, z0 = blockIdx.y * 64, tid = threadIdx.x;
+    const int kx = tid & 15, zr = tid >> 4;
+    for (int e = tid; e < 64 * 16; e += 256) {
+        const int a = e >> 4, k = e & 15;
+        sx[a][k] = (a < KZ && k < mx) ? in[((size_t)b * KZ + a) * mx + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < 64 * KZ; e += 256) {
         const int zz = e / KZ, a = e - zz * KZ;
         se[zz][a] = z0 + zz < Nz ? tz[(size_t)(z0 + zz) * KZ + a] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int o = tid; o < 32 * mx; o += 256) {
-        const int zz = o / mx, kx = o - zz * mx;
-        if (z0 + zz >= Nz) continue;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int a = 0; a < KZ; ++a) acc = cadd(acc, cmul(sx[a][kx], se[zz][a]));
-        out[((size_t)b * Nz + z0 + zz) * mx + kx] = acc;
+    float2 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int a = 0; a < KZ; ++a) {
+        const float2 y = sx[a][kx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = cadd(acc[q], cmul(y, se[zr + 16 * q][a]));
     }
+    if (kx < mx)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int z = z0 + zr + 16 * q;
+            if (z < Nz) out[((size_t)b * Nz + z) * mx + kx] = acc[q];
+        }
 }
 
 // --- per-mode channel mix ---------------------------------------------------------
@@ -196,7 +206,8 @@ __global__ void k_mix(int B, int Ci, int Co, int nm, const float2* __restrict__ 
     const long long bo = t / nm;
     const int o = (int)(bo % Co), b = (int)(bo / Co);
     float2 acc = make_float2(0.f, 0.f);
-    for (int i = 0; i < Ci; ++i)
+#pragma unroll 8
+    for (int i = 0; i < Ci; ++i)  // unrolled: eight loads of each operand in flight
         acc = cadd(acc, cmul(X[((size_t)b * Ci + i) * nm + m], R[((size_t)i * Co + o) * nm + m]));
     Y[t] = acc;
 }
@@ -210,6 +221,7 @@ __global__ void k_mix_dx(int B, int Ci, int Co, int nm, const float2* __restrict
     const long long bi = t / nm;
     const int i = (int)(bi % Ci), b = (int)(bi / Ci);
     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
     for (int o = 0; o < Co; ++o)
         acc = cadd(acc, cmulc(dY[((size_t)b * Co + o) * nm + m], R[((size_t)i * Co + o) * nm + m]));
     dX[t] = acc;
@@ -224,6 +236,7 @@ __global__ void k_mix_dr(int B, int Ci, int Co, int nm, const float2* __restrict
     const long long io = t / nm;
     const int o = (int)(io % Co), i = (int)(io / Co);
     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
     for (int b = 0; b < B; ++b)  // conj(X) dY, summed over the batch in order
         acc = cadd(acc, cmulc(dY[((size_t)b * Co + o) * nm + m], X[((size_t)b * Ci + i) * nm + m]));
     dR[t] = acc;
@@ -248,10 +261,12 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
     const int b = blockIdx.z, z = blockIdx.y, tid = threadIdx.x;
     const int x = blockIdx.x * 256 + tid;
     const int n2 = 2 * mx;
+#pragma unroll 4
     for (int e = tid; e < co * CIMAX; e += 256) {
         const int o = e / CIMAX, i = e - o * CIMAX;
         sM[e] = i < ci ? (mtrans ? M[(size_t)i * co + o] : M[(size_t)o * ci + i]) : 0.0f;
     }
+#pragma unroll 4
     for (int e = tid; e < co * 32; e += 256) {
         const int o = e >> 5, r = e & 31;
         sT[e] = (T && r < n2) ? T[(((size_t)b * co + o) * Nz + z) * n2 + r] : 0.0f;
@@ -783,47 +798,71 @@ __global__ void __launch_bounds__(256) k_project(int ci, int H, long long npix, 
 }
 
 // --- weight gradients ---------------------------------------------------------------
-// Block k sums its pixel range into partial[k][o][0..cip) (column ci is the
-// bias, fed by a constant 1); k_wgrad_reduce adds the blocks in index order.
-constexpr int kWgPx = 32, kWgChunk = 2048;
+// Block (k, b) sums pixels [k kWgChunk, (k+1) kWgChunk) of sample b into
+// partial[b nchunk + k][o][0..cip) (column ci is the bias, fed by a constant
+// 1); k_wgrad_reduce adds the blocks in index order.
+constexpr int kWgTile = 64, kWgChunk = 2048;
 
 __host__ __device__ inline int wg_cip(int ci) { return ((ci + 1) + 3) & ~3; }
-inline long long wg_blocks(int B, long long npix) { return (B * npix + kWgChunk - 1) / kWgChunk; }
+inline long long wg_chunks(long long npix) { return (npix + kWgChunk - 1) / kWgChunk; }
+inline long long wg_blocks(int B, long long npix) { return B * wg_chunks(npix); }
 
-__global__ void k_wgrad(int B, int ci, int co, long long npix, const float* __restrict__ dU,
-                        const float* __restrict__ in, float* __restrict__ partial)
+__global__ void k_wgrad(int ci, int co, long long npix, const float* __restrict__ dU, const float* __restrict__ in,
+                        float* __restrict__ partial)
 {
     extern __shared__ __align__(16) float sm[];
     const int cip = wg_cip(ci), g4 = cip / 4;
-    float* sD = sm;                       // [kWgPx][co + 1]
-    float* sI = sm + kWgPx * (co + 1);    // [kWgPx][cip]
-    const long long total = (long long)B * npix;
-    const long long g0 = (long long)blockIdx.x * kWgChunk, g1 = min(g0 + kWgChunk, total);
+    float* sD = sm;                         // [kWgTile][co + 1]
+    float* sI = sm + kWgTile * (co + 1);    // [kWgTile][cip]
+    const int b = blockIdx.y;
+    const long long p0 = (long long)blockIdx.x * kWgChunk, p1 = min(p0 + (long long)kWgChunk, npix);
+    const float* dUb = dU + (size_t)b * co * npix;
+    const float* inb = in + (size_t)b * ci * npix;
     const int tid = threadIdx.x, ntask = co * g4;
     // up to two (o, 4 i) tasks per thread
     float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    for (long long g = g0; g < g1; g += kWgPx) {
-        for (int e = tid; e < kWgPx * co; e += blockDim.x) {
-            const int oo = e / kWgPx, p = e - oo * kWgPx;
-            float val = 0.0f;
-            if (g + p < g1) {
-                const long long bb = (g + p) / npix, pp = (g + p) - bb * npix;
-                val = dU[((size_t)bb * co + oo) * npix + pp];
-            }
-            sD[p * (co + 1) + oo] = val;
-        }
-        for (int e = tid; e < kWgPx * cip; e += blockDim.x) {
-            const int ii = e / kWgPx, p = e - ii * kWgPx;
-            float val = 0.0f;
-            if (g + p < g1) {
-                if (ii < ci) {
-                    const long long bb = (g + p) / npix, pp = (g + p) - bb * npix;
-                    val = in[((size_t)bb * ci + ii) * npix + pp];
-                } else if (ii == ci) {
-                    val = 1.0f;
+    // 16-byte loads when every row of 4 pixels is aligned; the loads of a tile are
+    // issued together (unrolled) and only then scattered into shared memory
+    const bool vec = (npix & 3) == 0 && (reinterpret_cast<uintptr_t>(dU) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    const int nrow = co + cip, nld = nrow * (kWgTile / 4);  // (channel row, 4-pixel group) pieces
+    for (long long g = p0; g < p1; g += kWgTile) {
+        const int n = (int)min((long long)kWgTile, p1 - g);
+        if (vec) {
+            for (int e0 = tid; e0 < nld; e0 += 4 * blockDim.x) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * blockDim.x, r = e / (kWgTile / 4), p = 4 * (e % (kWgTile / 4));
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < nld && p < n) {
+                        if (r < co) v[u] = *reinterpret_cast<const float4*>(dUb + (size_t)r * npix + g + p);
+                        else if (r - co < ci) v[u] = *reinterpret_cast<const float4*>(inb + (size_t)(r - co) * npix + g + p);
+                        else if (r - co == ci) v[u] = make_float4(1.f, 1.f, 1.f, 1.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * blockDim.x, r = e / (kWgTile / 4), p = 4 * (e % (kWgTile / 4));
+                    if (e >= nld) continue;
+                    const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float x = p + j < n ? f[j] : 0.0f;  // rows end on a multiple of 4 here
+                        if (r < co) sD[(p + j) * (co + 1) + r] = x;
+                        else sI[(p + j) * cip + (r - co)] = x;
+                    }
                 }
             }
-            sI[p * cip + ii] = val;
+        } else {
+            for (int e = tid; e < kWgTile * co; e += blockDim.x) {
+                const int oo = e / kWgTile, p = e % kWgTile;
+                sD[p * (co + 1) + oo] = p < n ? dUb[(size_t)oo * npix + g + p] : 0.0f;
+            }
+            for (int e = tid; e < kWgTile * cip; e += blockDim.x) {
+                const int ii = e / kWgTile, p = e % kWgTile;
+                sI[p * cip + ii] = p < n ? (ii < ci ? inb[(size_t)ii * npix + g + p] : (ii == ci ? 1.0f : 0.0f)) : 0.0f;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -832,7 +871,7 @@ __global__ void k_wgrad(int B, int ci, int co, long long npix, const float* __re
             if (task >= ntask) continue;
             const int o = task / g4, i4 = task - o * g4;
 #pragma unroll 8
-            for (int p = 0; p < kWgPx; ++p) {
+            for (int p = 0; p < kWgTile; ++p) {
                 const float d = sD[p * (co + 1) + o];
                 const float4 a = *reinterpret_cast<const float4*>(&sI[p * cip + 4 * i4]);
                 acc[q].x = fmaf(d, a.x, acc[q].x);
@@ -843,12 +882,13 @@ __global__ void k_wgrad(int B, int ci, int co, long long npix, const float* __re
         }
         __syncthreads();
     }
+    const size_t blk = (size_t)b * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int task = tid + q * (int)blockDim.x;
         if (task >= ntask) continue;
         const int o = task / g4, i4 = task - o * g4;
-        *reinterpret_cast<float4*>(&partial[((size_t)blockIdx.x * co + o) * cip + 4 * i4]) = acc[q];
+        *reinterpret_cast<float4*>(&partial[(blk * co + o) * cip + 4 * i4]) = acc[q];
     }
 }
 
@@ -1058,7 +1098,7 @@ wave_status_t fno_dft_z(int nb, int Nz, int mz, int mx, const float* in, const f
 {
     if (nb < 0 || !modes_ok(Nz, 2 * mx, mz, mx) || !in || !tz || !out) return WAVE_ERR_ARG;
     if (nb == 0) return WAVE_OK;
-    k_dft_z<<<nb, 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
+    k_dft_z<<<dim3(nb, (2 * mz + 7) / 8), 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
                                                   reinterpret_cast<const float2*>(tz), reinterpret_cast<float2*>(out));
     return launched();
 }
@@ -1067,7 +1107,7 @@ wave_status_t fno_idft_z(int nb, int Nz, int mz, int mx, const float* in, const 
 {
     if (nb < 0 || !modes_ok(Nz, 2 * mx, mz, mx) || !in || !tz || !out) return WAVE_ERR_ARG;
     if (nb == 0) return WAVE_OK;
-    dim3 grid(nb, (Nz + 31) / 32);
+    dim3 grid(nb, (Nz + 63) / 64);
     k_idft_z<<<grid, 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
                                                      reinterpret_cast<const float2*>(tz),
                                                      reinterpret_cast<float2*>(out));
@@ -1200,12 +1240,13 @@ wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, 
         return WAVE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const long long nblk = wg_blocks(B, npix);
-    if (nblk > 0x7fffffffLL) return WAVE_ERR_ARG;
+    if (nblk > 0x7fffffffLL || B > 65535) return WAVE_ERR_ARG;
     if (nblk > 0) {
         const int ntask = Co * (wg_cip(Ci) / 4);
         const int threads = std::min(1024, (((ntask + 1) / 2 + 31) / 32) * 32);
-        const size_t smem = (size_t)(kWgPx * (Co + 1) + kWgPx * wg_cip(Ci)) * sizeof(float);
-        k_wgrad<<<(unsigned)nblk, threads, smem, s>>>(B, Ci, Co, npix, dU, in, work);
+        const size_t smem = (size_t)(kWgTile * (Co + 1) + kWgTile * wg_cip(Ci)) * sizeof(float);
+        const dim3 grid((unsigned)wg_chunks(npix), B);
+        k_wgrad<<<grid, threads, smem, s>>>(Ci, Co, npix, dU, in, work);
     }
     const int nout = Co * (Ci + 1);
     k_wgrad_reduce<<<(nout + 255) / 256, 256, 0, s>>>(Ci, Co, nblk, work, dM, dbias);
