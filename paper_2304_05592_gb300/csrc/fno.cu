@@ -398,6 +398,8 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int sr
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// all but the kDxtStages - 1 most recent groups complete (kDxtStages = 3)
+__device__ __forceinline__ void cp_async_wait_stages() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 // GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2 with erf from Abramowitz and
 // Stegun, Handbook of Mathematical Functions, formula 7.1.26 (after Hastings):
@@ -763,6 +765,130 @@ __global__ void __launch_bounds__(128) k_dft_x_tc(long long rows, int Nx, int n2
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tm) : "memory");
 }
 
+// The same x transform with the activations streamed through a kDxtStages-deep
+// cp.async ring (Nx a multiple of 8): each 64-wide K chunk of the 128-row tile
+// is copied in 16-byte pieces, a quarter-warp filling 128 contiguous bytes of
+// shared memory (rows 8 g .. 8 g + 7 of one 8-column group), while the MMAs of
+// earlier chunks run.  The table chunk (BF16, K-major) is double-buffered: its
+// floats are loaded into registers one chunk ahead and stored just before the
+// chunk's MMAs.  A stage is refilled once the MMAs that read it have committed.
+constexpr int kDxtStages = 3;
+constexpr int kDxtSA = 128 * kTcKc * 2, kDxtSB = 32 * kTcKc * 2;  // bytes per A stage, per B buffer
+constexpr int kDxtSmem = kDxtStages * kDxtSA + 2 * kDxtSB;
+
+__global__ void __launch_bounds__(128) k_dft_x_tc2(long long rows, int Nx, int n2, const __nv_bfloat16* __restrict__ in,
+                                                   const float* __restrict__ tab, float* __restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* const sA = smem;                          // [kDxtStages][kDxtSA]
+    unsigned char* const sB = smem + kDxtStages * kDxtSA;    // [2][kDxtSB]
+    __shared__ __align__(8) uint64_t bar[kDxtStages];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long r0 = (long long)blockIdx.x * 128;
+    const int nchunk = (Nx + kTcKc - 1) / kTcKc;
+
+    if (tid == 0) {
+        for (int j = 0; j < kDxtStages; ++j)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[j])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(su32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // chunk c -> stage c % kDxtStages: piece (g, kg, r8) = rows 8 g + r8, x = 64 c + 8 kg .. + 7
+    auto issue_chunk = [&](int c) {
+        if (c < nchunk) {
+            unsigned char* a = sA + (c % kDxtStages) * kDxtSA;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = tid + 128 * u, r8 = e & 7, kg = (e >> 3) & 7, g = e >> 6;
+                const long long gr = r0 + 8 * g + r8;
+                const int x = c * kTcKc + 8 * kg;
+                const bool ok = gr < rows && x < Nx;
+                const __nv_bfloat16* src = in + (ok ? gr * Nx + x : 0);
+                cp_async16(su32(a + g * 1024 + kg * 128 + r8 * 16), src, ok ? 16 : 0);
+            }
+        }
+        cp_async_commit();  // one group per chunk slot, empty past the end
+    };
+    // table chunk c: thread owns pieces (n, kg) = (tid & 31, 2 (tid >> 5) + {0, 1}), 8 x each
+    float tb[2][8];
+    auto load_table = [&](int c) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int n = tid & 31, kg = 2 * (tid >> 5) + q;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int x = c * kTcKc + 8 * kg + j;
+                tb[q][j] = (c < nchunk && n < n2 && x < Nx) ? tab[(size_t)x * n2 + n] : 0.0f;
+            }
+        }
+    };
+    auto store_table = [&](int c) {
+        unsigned char* bb = sB + (c & 1) * kDxtSB;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int n = tid & 31, kg = 2 * (tid >> 5) + q;
+            *reinterpret_cast<uint4*>(bb + (n >> 3) * 1024 + kg * 128 + (n & 7) * 16) = pack8_bf16(tb[q]);
+        }
+    };
+#pragma unroll
+    for (int c = 0; c < kDxtStages; ++c) issue_chunk(c);
+    load_table(0);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    bool ok = true;
+    uint32_t tm = 0;
+    for (int c = 0; c < nchunk; ++c) {
+        const int st = c % kDxtStages;
+        store_table(c);  // buffer c & 1 was last read by chunk c - 2's MMAs, waited for below
+        cp_async_wait_stages();  // this thread's pieces of chunk c have landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tm = tmem_base;
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < kTcKc / 16; ++j)
+                umma_bf16(tm, umma_desc_sbo(su32(sA + st * kDxtSA) + j * 256, 1024),
+                          umma_desc_sbo(su32(sB + (c & 1) * kDxtSB) + j * 256, 1024), idesc, (c > 0 || j > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&bar[st]))
+                         : "memory");
+        }
+        if (c + 1 < nchunk) load_table(c + 1);  // in flight during the wait below
+        // chunk c's MMAs done: stage st may be refilled and table buffer c & 1 rewritten
+        ok = mbar_wait_parity(&bar[st], (uint32_t)(c / kDxtStages) & 1u) && ok;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issue_chunk(c + kDxtStages);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+        float v[32];
+        tmem_ld32(tm + ((uint32_t)(warp * 32) << 16), v);
+        const long long r = r0 + warp * 32 + lane;
+        if (r < rows) {
+            if ((n2 & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+#pragma unroll
+                for (int n = 0; n < 32; n += 4)
+                    if (n < n2) *reinterpret_cast<float4*>(out + r * n2 + n) = make_float4(v[n], v[n + 1], v[n + 2], v[n + 3]);
+            } else {
+#pragma unroll
+                for (int n = 0; n < 32; ++n)
+                    if (n < n2) out[r * n2 + n] = v[n];
+            }
+        }
+    } else if (lane == 0) {
+        atomicOr(&g_tc_err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tm) : "memory");
+}
+
 // --- projection head on the CUDA cores ------------------------------------------------
 // out[b][p] = q2 + sum_h Q2[h] GELU(q1[h] + sum_i Q1[h][i] in[b][i][p]): the
 // two pointwise layers of the head in one pass, the hidden channels kept in
@@ -1082,8 +1208,21 @@ wave_status_t fno_dft_x(long long rows, int Nx, int mx, const void* in, int in_b
     if (nblk > 0x7fffffffLL) return WAVE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (in_bf16 && g_tensor_cores) {
-        k_dft_x_tc<<<(unsigned)nblk128(rows), 128, 0, s>>>(rows, Nx, 2 * mx, static_cast<const __nv_bfloat16*>(in),
-                                                           table, out);
+        if ((Nx & 7) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+            static bool attr[64] = {false};  // per device
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WAVE_ERR_CUDA;
+            if (!attr[dev]) {
+                if (cudaFuncSetAttribute(k_dft_x_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, kDxtSmem) != cudaSuccess)
+                    return WAVE_ERR_CUDA;
+                attr[dev] = true;
+            }
+            k_dft_x_tc2<<<(unsigned)nblk128(rows), 128, kDxtSmem, s>>>(
+                rows, Nx, 2 * mx, static_cast<const __nv_bfloat16*>(in), table, out);
+        } else {
+            k_dft_x_tc<<<(unsigned)nblk128(rows), 128, 0, s>>>(rows, Nx, 2 * mx, static_cast<const __nv_bfloat16*>(in),
+                                                               table, out);
+        }
         return launched();
     }
     if (in_bf16)

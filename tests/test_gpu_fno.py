@@ -215,10 +215,13 @@ def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nz, 
     assert rel(out_tc, out_cc) < 1e-2
 
 
-@pytest.mark.parametrize("shape", [(2, 32, 24, 512, 16), (3, 5, 37, 300, 7)])
+@pytest.mark.parametrize("shape", [(2, 32, 24, 512, 16), (3, 5, 37, 300, 7), (3, 5, 37, 264, 8), (1, 2, 40, 1024, 16),
+                                   (1, 3, 20, 1032, 5)])
 def test_tensor_core_x_transform_matches_reference(shape):
     """The tcgen05 x transform of BF16 activations (K = Nx in chunks of 64,
-    ragged K and rows) against the CUDA-core kernel and an FP64 reference."""
+    ragged K and rows; rows of a multiple of 8 through the cp.async ring, others
+    through the staged kernel) against the CUDA-core kernel and an FP64
+    reference."""
     B, C, Nz, Nx, mx = shape
     v = torch.from_numpy(RNG.standard_normal((B, C, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
     (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, 4, mx)
