@@ -39,8 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # time; a kernel whose source has changed since gets null.
 VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,fwd>"),
                   (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,adj>")}
-TRAFFIC = {("k_step2d_sgt<16,8,2,fwd>", "9498ac26b2994f47"): 82.00e6,
-           ("k_step2d_sgt<16,8,2,adj>", "9498ac26b2994f47"): 91.66e6,
+TRAFFIC = {("k_step2d_sgt<16,8,2,fwd>", "3397d6944cc152dd"): 82.22e6,
+           ("k_step2d_sgt<16,8,2,adj>", "3397d6944cc152dd"): 91.71e6,
            ("k_step3d_tma<8,64,10,fwd>", "ff84bd7b5179962b"): 1434.45e6}
 
 
