@@ -78,6 +78,14 @@ wave_status_t fno_idft_z(int nb, int Nz, int mz, int mx, const float* in, const 
 wave_status_t fno_mix(int B, int Ci, int Co, int nmode, const float* X, const float* R, float* Y,
                       void* stream);
 
+/* fno_mix followed by fno_idft_z in one pass, the mixed spectrum Y kept on chip:
+ *   out[b][o][z][kx] = sum_a Y[b][o][a][kx] E[z][a],
+ *   Y[b][o][a][kx]   = sum_i X[b][i][a][kx] R[i][o][a][kx]
+ * with a over the 2 mz kept z modes (X [B][Ci][2mz][mx][2], R as in fno_mix,
+ * out [B][Co][Nz][mx][2]).  Both sums run in the order of the separate calls. */
+wave_status_t fno_mix_idft_z(int B, int Ci, int Co, int Nz, int mz, int mx, const float* X, const float* R,
+                             const float* tz, float* out, void* stream);
+
 /* Its backward: dX[b][i][m] = sum_o dY[b][o][m] conj(R[i][o][m]) and
  * dR[i][o][m] = sum_b conj(X[b][i][m]) dY[b][o][m] (dR overwritten; the sum
  * over b runs in a fixed order).  Either output may be NULL. */

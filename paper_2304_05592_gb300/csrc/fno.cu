@@ -212,6 +212,54 @@ __global__ void k_mix(int B, int Ci, int Co, int nm, const float2* __restrict__ 
     Y[t] = acc;
 }
 
+// k_mix followed by k_idft_z for one (b, o) per CTA, the mixed spectrum kept in
+// shared memory: out[b][o][z][kx] = sum_a Y[a][kx] E[z][a] with
+// Y[a][kx] = sum_i X[b][i][a][kx] R[i][o][a][kx] (both sums in the same order as
+// the two separate kernels).
+__global__ void __launch_bounds__(256) k_mix_idft_z(int Ci, int Co, int Nz, int KZ, int mx, const float2* __restrict__ X,
+                                                    const float2* __restrict__ R, const float2* __restrict__ tz,
+                                                    float2* __restrict__ out)
+{
+    __shared__ float2 sy[64][16];
+    __shared__ float2 se[64][65];
+    const int bo = blockIdx.x, b = bo / Co, o = bo - b * Co, tid = threadIdx.x;
+    const int nm = KZ * mx;
+    for (int m = tid; m < 64 * 16; m += 256) {
+        const int a = m >> 4, k = m & 15;
+        float2 acc = make_float2(0.f, 0.f);
+        if (a < KZ && k < mx) {
+            const int mm = a * mx + k;
+#pragma unroll 8
+            for (int i = 0; i < Ci; ++i)
+                acc = cadd(acc, cmul(X[((size_t)b * Ci + i) * nm + mm], R[((size_t)i * Co + o) * nm + mm]));
+        }
+        sy[a][k] = acc;
+    }
+    const int kx = tid & 15, zr = tid >> 4;
+    for (int z0 = 0; z0 < Nz; z0 += 64) {
+        __syncthreads();  // the spectrum is complete; the previous chunk's table has been read
+        for (int e = tid; e < 64 * KZ; e += 256) {
+            const int zz = e / KZ, a = e - zz * KZ;
+            se[zz][a] = z0 + zz < Nz ? tz[(size_t)(z0 + zz) * KZ + a] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float2 acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int a = 0; a < KZ; ++a) {
+            const float2 y = sy[a][kx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = cadd(acc[q], cmul(y, se[zr + 16 * q][a]));
+        }
+        if (kx < mx)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int z = z0 + zr + 16 * q;
+                if (z < Nz) out[((size_t)bo * Nz + z) * mx + kx] = acc[q];
+            }
+    }
+}
+
 __global__ void k_mix_dx(int B, int Ci, int Co, int nm, const float2* __restrict__ dY, const float2* __restrict__ R,
                          float2* __restrict__ dX)
 {
@@ -1261,6 +1309,20 @@ wave_status_t fno_mix(int B, int Ci, int Co, int nmode, const float* X, const fl
     k_mix<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         B, Ci, Co, nmode, reinterpret_cast<const float2*>(X), reinterpret_cast<const float2*>(R),
         reinterpret_cast<float2*>(Y));
+    return launched();
+}
+
+wave_status_t fno_mix_idft_z(int B, int Ci, int Co, int Nz, int mz, int mx, const float* X, const float* R,
+                             const float* tz, float* out, void* stream)
+{
+    if (B < 0 || Ci < 1 || Co < 1 || Ci > 64 || Co > 64 || !modes_ok(Nz, 2 * mx, mz, mx) || !X || !R || !tz || !out)
+        return WAVE_ERR_ARG;
+    const long long nb = (long long)B * Co;
+    if (nb == 0) return WAVE_OK;
+    if (nb > 0x7fffffffLL) return WAVE_ERR_ARG;
+    k_mix_idft_z<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(
+        Ci, Co, Nz, 2 * mz, mx, reinterpret_cast<const float2*>(X), reinterpret_cast<const float2*>(R),
+        reinterpret_cast<const float2*>(tz), reinterpret_cast<float2*>(out));
     return launched();
 }
 

@@ -41,6 +41,7 @@ def _lib():
             "fno_idft_z": [I, I, I, I, P, P, P, P],
             "fno_mix": [I, I, I, I, P, P, P, P],
             "fno_mix_backward": [I, I, I, I, P, P, P, P, P, P],
+            "fno_mix_idft_z": [I, I, I, I, I, I, P, P, P, P, P],
             "fno_combine": [I, I, I, I, I, I, P, I, P, I, P, P, P, I, P, P, I, P],
             "fno_project": [I, I, I, I, I, P, I, P, P, P, P, P, P],
             "fno_wgrad": [I, I, I, L, P, P, P, P, P, P],
@@ -119,6 +120,14 @@ def fno_mix(X, R, B, Ci, Co, nmode, out=None, stream=None):
     if out is None:
         out = torch.empty((B, Co, nmode, 2), dtype=torch.float32, device=X.device)
     _call("fno_mix", B, Ci, Co, nmode, _p(X), _p(R), _p(out), _s(stream))
+    return out
+
+
+def fno_mix_idft_z(X, R, B, Ci, Co, Nz, mz, mx, tz, out=None, stream=None):
+    """fno_mix then fno_idft_z in one pass: [B][Co][Nz][mx][2] from X [B][Ci][2mz][mx][2]."""
+    if out is None:
+        out = torch.empty((B * Co, Nz, mx, 2), dtype=torch.float32, device=X.device)
+    _call("fno_mix_idft_z", B, Ci, Co, Nz, mz, mx, _p(X), _p(R), _p(tz), _p(out), _s(stream))
     return out
 
 
@@ -289,8 +298,7 @@ class FNO2d:
             last = l == cfg.layers - 1
             T1 = fno_dft_x(v, mx, self.tx_fwd)
             X = fno_dft_z(T1, B * W, Nz, mz, mx, self.tz)
-            Y = fno_mix(X, self.view(f"R{l}"), B, W, W, KZ * mx)
-            T2 = fno_idft_z(Y, B * W, Nz, mz, mx, self.tz)
+            T2 = fno_mix_idft_z(X, self.view(f"R{l}"), B, W, W, Nz, mz, mx, self.tz)
             pre = torch.empty((B, W, Nz, Nx), dtype=torch.float32, device=x.device) if (train and not last) else None
             vn = fno_combine(v, self.view(f"W{l}"), W, bias=self.view(f"b{l}"), T=T2, table=self.tx_inv, mx=mx,
                              act=ACT_NONE if last else ACT_GELU, pre=pre, out_dtype=adt)

@@ -67,6 +67,28 @@ def test_truncated_dft_and_inverse(shape):
     assert rel(dv.cpu().numpy(), ofno.dft_trunc_adjoint(Y, Nz, Nx)) < TOL
 
 
+@pytest.mark.parametrize("B,Ci,Co,Nz,mz,mx", [(2, 32, 32, 256, 16, 16), (3, 5, 7, 37, 3, 5), (1, 4, 64, 130, 32, 9)])
+def test_fused_mix_and_inverse_z(B, Ci, Co, Nz, mz, mx):
+    """fno_mix_idft_z against fno_mix followed by fno_idft_z, and against both
+    sums evaluated in FP64 (einsum) with the same z table."""
+    KZ = 2 * mz
+    X = RNG.standard_normal((B, Ci, KZ, mx, 2))
+    R = RNG.standard_normal((Ci, Co, KZ, mx, 2))
+    _, tz = fno.fno_tables(Nz, 2 * mx, mz, mx)
+    fused = fno.fno_mix_idft_z(dev(X), dev(R), B, Ci, Co, Nz, mz, mx, tz).cpu().numpy()
+    Y = fno.fno_mix(dev(X), dev(R), B, Ci, Co, KZ * mx)
+    two = fno.fno_idft_z(Y, B * Co, Nz, mz, mx, tz).cpu().numpy()
+    assert rel(fused, two) < 1e-6
+    Xc = X[..., 0] + 1j * X[..., 1]
+    Rc = R[..., 0] + 1j * R[..., 1]
+    Yc = np.einsum("biam,ioam->boam", Xc, Rc)
+    E = tz.cpu().numpy().astype(np.float64)
+    Ec = E[..., 0] + 1j * E[..., 1]  # [Nz][KZ]
+    ref = np.einsum("boam,za->bozm", Yc, Ec)
+    fc = fused.reshape(B, Co, Nz, mx, 2)
+    assert rel(fc[..., 0] + 1j * fc[..., 1], ref) < 1e-5
+
+
 def test_mode_mix_and_backward():
     B, Ci, Co, KZ, mx = 3, 5, 7, 8, 6
     X = RNG.standard_normal((B, Ci, KZ, mx)) + 1j * RNG.standard_normal((B, Ci, KZ, mx))
