@@ -121,43 +121,64 @@ __global__ void __launch_bounds__(256) k_dft_x(long long rows, int Nx, int n2, c
 
 // --- along z -------------------------------------------------------------------
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
-{
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// acc + a b and acc + a conj(b) as four FMAs each
+__device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b)
+{
+    return make_float2(fmaf(-a.y, b.y, fmaf(a.x, b.x, acc.x)), fmaf(a.y, b.x, fmaf(a.x, b.y, acc.y)));
+}
+__device__ __forceinline__ float2 cfmac(float2 acc, float2 a, float2 b)
+{
+    return make_float2(fmaf(a.y, b.y, fmaf(a.x, b.x, acc.x)), fmaf(-a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
 
-// out[b][a][kx] = sum_z in[b][z][kx] conj(E[z][a]); CTA per (b, 8 values of a).
-// Thread (h, al, kx): output (a0 + al, kx), half h of every 64-row chunk of z;
-// the two halves are added at the end (always in the same order).
+// out[b][a][kx] = sum_z in[b][z][kx] conj(E[z][a]); CTA per (b, 16 values of a).
+// Thread (h, q, kx) computes outputs (a0 + 4 q .. a0 + 4 q + 3, kx) over quarter h
+// of every 64-row chunk of z, so each in[z][kx] read from shared memory feeds
+// four outputs; the quarters are added at the end in a fixed order.
 __global__ void __launch_bounds__(256) k_dft_z(int Nz, int KZ, int mx, const float2* __restrict__ in,
                                                const float2* __restrict__ tz, float2* __restrict__ out)
 {
     __shared__ float2 si[64][16];
-    __shared__ float2 se[64][8];
-    __shared__ float2 red[8][16];
-    const int b = blockIdx.x, a0 = blockIdx.y * 8, tid = threadIdx.x;
-    const int kx = tid & 15, al = (tid >> 4) & 7, h = tid >> 7;
-    float2 acc = make_float2(0.f, 0.f);
+    __shared__ __align__(16) float2 se[64][16];
+    __shared__ float2 red[3][16][16];
+    const int b = blockIdx.x, a0 = blockIdx.y * 16, tid = threadIdx.x;
+    const int kx = tid & 15, q = (tid >> 4) & 3, h = tid >> 6;
+    float2 acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.f, 0.f);
     for (int z0 = 0; z0 < Nz; z0 += 64) {
         const int zc = min(64, Nz - z0);
         for (int e = tid; e < 64 * 16; e += 256) {
             const int zz = e >> 4, k = e & 15;
             si[zz][k] = (zz < zc && k < mx) ? in[((size_t)b * Nz + z0 + zz) * mx + k] : make_float2(0.f, 0.f);
-        }
-        for (int e = tid; e < 64 * 8; e += 256) {
-            const int zz = e >> 3, a = e & 7;
-            se[zz][a] = (zz < zc && a0 + a < KZ) ? tz[(size_t)(z0 + zz) * KZ + a0 + a] : make_float2(0.f, 0.f);
+            se[zz][k] = (zz < zc && a0 + k < KZ) ? tz[(size_t)(z0 + zz) * KZ + a0 + k] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int zz = 32 * h; zz < 32 * h + 32; ++zz) acc = cadd(acc, cmulc(si[zz][kx], se[zz][al]));
+#pragma unroll 4
+        for (int zz = 16 * h; zz < 16 * h + 16; ++zz) {
+            const float2 v = si[zz][kx];
+            const float4 e01 = *reinterpret_cast<const float4*>(&se[zz][4 * q]);
+            const float4 e23 = *reinterpret_cast<const float4*>(&se[zz][4 * q + 2]);
+            acc[0] = cfmac(acc[0], v, make_float2(e01.x, e01.y));
+            acc[1] = cfmac(acc[1], v, make_float2(e01.z, e01.w));
+            acc[2] = cfmac(acc[2], v, make_float2(e23.x, e23.y));
+            acc[3] = cfmac(acc[3], v, make_float2(e23.z, e23.w));
+        }
         __syncthreads();
     }
-    if (h == 1) red[al][kx] = acc;
+    if (h > 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[h - 1][4 * q + j][kx] = acc[j];
     __syncthreads();
-    if (h == 0 && kx < mx && a0 + al < KZ) out[((size_t)b * KZ + a0 + al) * mx + kx] = cadd(acc, red[al][kx]);
+    if (h == 0 && kx < mx)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int aa = a0 + 4 * q + j;
+            if (aa < KZ)
+                out[((size_t)b * KZ + aa) * mx + kx] =
+                    cadd(cadd(acc[j], red[0][4 * q + j][kx]), cadd(red[1][4 * q + j][kx], red[2][4 * q + j][kx]));
+        }
 }
 
 // out[b][z][kx] = sum_a in[b][a][kx] E[z][a]; CTA per (b, 64 rows of z).
@@ -185,7 +206,7 @@ __global__ void __launch_bounds__(256) k_idft_z(int Nz, int KZ, int mx, const fl
     for (int a = 0; a < KZ; ++a) {
         const float2 y = sx[a][kx];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = cadd(acc[q], cmul(y, se[zr + 16 * q][a]));
+        for (int q = 0; q < 4; ++q) acc[q] = cfma(acc[q], y, se[zr + 16 * q][a]);
     }
     if (kx < mx)
 #pragma unroll
@@ -208,7 +229,7 @@ __global__ void k_mix(int B, int Ci, int Co, int nm, const float2* __restrict__ 
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int i = 0; i < Ci; ++i)  // unrolled: eight loads of each operand in flight
-        acc = cadd(acc, cmul(X[((size_t)b * Ci + i) * nm + m], R[((size_t)i * Co + o) * nm + m]));
+        acc = cfma(acc, X[((size_t)b * Ci + i) * nm + m], R[((size_t)i * Co + o) * nm + m]);
     Y[t] = acc;
 }
 
@@ -231,7 +252,7 @@ __global__ void __launch_bounds__(256) k_mix_idft_z(int Ci, int Co, int Nz, int 
             const int mm = a * mx + k;
 #pragma unroll 8
             for (int i = 0; i < Ci; ++i)
-                acc = cadd(acc, cmul(X[((size_t)b * Ci + i) * nm + mm], R[((size_t)i * Co + o) * nm + mm]));
+                acc = cfma(acc, X[((size_t)b * Ci + i) * nm + mm], R[((size_t)i * Co + o) * nm + mm]);
         }
         sy[a][k] = acc;
     }
@@ -249,7 +270,7 @@ __global__ void __launch_bounds__(256) k_mix_idft_z(int Ci, int Co, int Nz, int 
         for (int a = 0; a < KZ; ++a) {
             const float2 y = sy[a][kx];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = cadd(acc[q], cmul(y, se[zr + 16 * q][a]));
+            for (int q = 0; q < 4; ++q) acc[q] = cfma(acc[q], y, se[zr + 16 * q][a]);
         }
         if (kx < mx)
 #pragma unroll
@@ -271,7 +292,7 @@ __global__ void k_mix_dx(int B, int Ci, int Co, int nm, const float2* __restrict
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int o = 0; o < Co; ++o)
-        acc = cadd(acc, cmulc(dY[((size_t)b * Co + o) * nm + m], R[((size_t)i * Co + o) * nm + m]));
+        acc = cfmac(acc, dY[((size_t)b * Co + o) * nm + m], R[((size_t)i * Co + o) * nm + m]);
     dX[t] = acc;
 }
 
@@ -286,7 +307,7 @@ __global__ void k_mix_dr(int B, int Ci, int Co, int nm, const float2* __restrict
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int b = 0; b < B; ++b)  // conj(X) dY, summed over the batch in order
-        acc = cadd(acc, cmulc(dY[((size_t)b * Co + o) * nm + m], X[((size_t)b * Ci + i) * nm + m]));
+        acc = cfmac(acc, dY[((size_t)b * Co + o) * nm + m], X[((size_t)b * Ci + i) * nm + m]);
     dR[t] = acc;
 }
 
@@ -1285,7 +1306,7 @@ wave_status_t fno_dft_z(int nb, int Nz, int mz, int mx, const float* in, const f
 {
     if (nb < 0 || !modes_ok(Nz, 2 * mx, mz, mx) || !in || !tz || !out) return WAVE_ERR_ARG;
     if (nb == 0) return WAVE_OK;
-    k_dft_z<<<dim3(nb, (2 * mz + 7) / 8), 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
+    k_dft_z<<<dim3(nb, (2 * mz + 15) / 16), 256, 0, (cudaStream_t)stream>>>(Nz, 2 * mz, mx, reinterpret_cast<const float2*>(in),
                                                   reinterpret_cast<const float2*>(tz), reinterpret_cast<float2*>(out));
     return launched();
 }
