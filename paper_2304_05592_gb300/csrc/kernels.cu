@@ -720,12 +720,13 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
                 for (int e = 0; e < 4; ++e) g[e] -= uf[e] * (out[e] - 2.0f * cen[e] + um[e]);
             }
         }
-        __syncthreads();  // the stage has been read and this shot's points are written
+        // This CTA's taps for the shot (the same values in every thread, so the
+        // decisions below are uniform over the CTA).
+        int ib = 0, ie = 0, gb = 0, ge = 0;
         if (sparse) {
             const int kcell = TZ / a.TZc;
             const int cbase = (shot * a.ncx + (int)blockIdx.x) * a.ncz;
             const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
-            int ib = 0, ie = 0, gb = 0, ge = 0;
             if (a.inj.cell_start) {
                 ib = a.inj.cell_start[cbase + c0];
                 ie = a.inj.cell_start[cbase + c1];
@@ -734,6 +735,11 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
                 gb = a.gat.cell_start[cbase + c0];
                 ge = a.gat.cell_start[cbase + c1];
             }
+        }
+        const bool taps = ie > ib || ge > gb;
+        // the stage is refilled by shot i + 2's copies, and taps touch other threads' points
+        if (taps || i + 2 < ns) __syncthreads();
+        if (taps) {
             sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * BZ, imaging ? sg : nullptr, z0, x0);
             if (imaging) __syncthreads();  // injection terms land in the gradient tile before the next shot
         }
