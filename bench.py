@@ -37,10 +37,12 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (kernel, SHA-256 prefix of that kernel's source text plus the shared stencil header) at capture
 # time; a kernel whose source has changed since gets null.
-VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,fwd>"),
-                  (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,adj>")}
-TRAFFIC = {("k_step2d_sgt<16,8,2,fwd>", "3397d6944cc152dd"): 82.22e6,
-           ("k_step2d_sgt<16,8,2,adj>", "3397d6944cc152dd"): 91.71e6,
+VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,fwd>"),
+                  (0, 27): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,fwd>"),
+                  (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>")}
+TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "4769d877bd0ca510"): 81.82e6,
+           ("k_step2d_sgt<16,8,2,1,fwd>", "4769d877bd0ca510"): 81.12e6,
+           ("k_step2d_sgt<16,8,2,0,adj>", "4769d877bd0ca510"): 92.24e6,
            ("k_step3d_tma<8,64,10,fwd>", "ff84bd7b5179962b"): 1434.45e6}
 
 
