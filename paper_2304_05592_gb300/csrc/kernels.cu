@@ -627,9 +627,14 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
         }
     }
 
+    // A thread whose wait for a stage gives up records the timeout and does no
+    // further work, but passes every block barrier below (they are uniform), so
+    // the CTA never splits; thread 0, which issues the copies, first waits
+    // (bounded) for the two it has in flight and issues no more.
+    bool alive = true;
     for (int i = 0; i < ns; ++i) {
         const int shot = s0 + i, stage = i & 1;
-        if (tid == 0 && i + 1 < ns) {
+        if (tid == 0 && alive && i + 1 < ns) {
             fence_proxy_async();
             mbar_expect_tx(&bar[stage ^ 1], kBytes);
             tma_load_4d(st + (stage ^ 1) * SU2, mh, &bar[stage ^ 1], x0 - 4, z0 - 4, shot + 1, a.u_buf);
@@ -643,23 +648,23 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
                 uo[rr] = live[rr] ? *reinterpret_cast<const float4*>(a.uprev + so + off[rr])
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const bool ok = mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
-        if (__syncthreads_or(!ok)) {
+        if (alive && !mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u)) {
+            alive = false;
+            atomicOr(a.err, kErrTimeout);
             if (tid == 0) {
-                atomicOr(a.err, kErrTimeout);
                 // copies issued by this CTA may still land in its shared memory
                 mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
                 if (i + 1 < ns) mbar_wait(&bar[stage ^ 1], (uint32_t)((i + 1) >> 1) & 1u);
             }
-            return;
         }
         const float* sb = st + stage * SU2;
-        if (PT) {
+        if (PT && alive) {
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) uo[rr] = lds4(sb + SU + (ty + rr * BZ) * kTX + lx);
         }
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr) {
+            if (!alive) break;
             const int r = ty + rr * BZ;
             float* un = a.unew + so + off[rr];
             if (!live[rr]) {
