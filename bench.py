@@ -39,10 +39,12 @@ FALLBACK_HBM_GBS = 6800.0
 # time; a kernel whose source has changed since gets null.
 VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,fwd>"),
                   (0, 27): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,fwd>"),
-                  (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>")}
-TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "4769d877bd0ca510"): 81.82e6,
-           ("k_step2d_sgt<16,8,2,1,fwd>", "4769d877bd0ca510"): 81.12e6,
-           ("k_step2d_sgt<16,8,2,0,adj>", "4769d877bd0ca510"): 92.24e6,
+                  (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>"),
+                  (1, 25): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,adj>")}
+TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "975aabe1792167d4"): 81.84e6,
+           ("k_step2d_sgt<16,8,2,1,fwd>", "975aabe1792167d4"): 81.89e6,
+           ("k_step2d_sgt<16,8,2,0,adj>", "975aabe1792167d4"): 93.86e6,
+           ("k_step2d_sgt<16,8,2,1,adj>", "975aabe1792167d4"): 94.70e6,
            ("k_step3d_tma<8,64,10,fwd>", "ff84bd7b5179962b"): 1434.45e6}
 
 
