@@ -372,6 +372,70 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
     }
 }
 
+// The same channel mix for few input channels and no spectral term (the lift):
+// each thread takes 4 consecutive pixels of one sample (16-byte input loads) and
+// writes 4 pixels of every output channel at once; the sum over i runs in the
+// order of k_combine, so results are identical.  Needs Nz Nx a multiple of 4.
+template <int CIMAX, typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_combine_px4(int ci, int co, long long npix, const Tin* __restrict__ in,
+                                                     const float* __restrict__ M, int mtrans,
+                                                     const float* __restrict__ bias, int act, float* __restrict__ pre,
+                                                     Tout* __restrict__ out)
+{
+    __shared__ float sM[64][CIMAX];
+    __shared__ float sB[64];
+    const int tid = threadIdx.x, b = blockIdx.y;
+    for (int e = tid; e < co * CIMAX; e += 256) {
+        const int o = e / CIMAX, i = e - o * CIMAX;
+        sM[o][i] = i < ci ? (mtrans ? M[(size_t)i * co + o] : M[(size_t)o * ci + i]) : 0.0f;
+    }
+    for (int o = tid; o < co; o += 256) sB[o] = bias ? bias[o] : 0.0f;
+    __syncthreads();
+    const long long p = 4 * ((long long)blockIdx.x * 256 + tid);
+    if (p >= npix) return;  // no barrier follows
+    float v[CIMAX][4];
+#pragma unroll
+    for (int i = 0; i < CIMAX; ++i) {
+        if (i < ci) {
+            const size_t base = ((size_t)b * ci + i) * npix + p;
+            if constexpr (sizeof(Tin) == 4) {
+                const float4 t = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(in) + base);
+                v[i][0] = t.x, v[i][1] = t.y, v[i][2] = t.z, v[i][3] = t.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[i][q] = ldf(in, base + q);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[i][q] = 0.0f;
+        }
+    }
+    for (int o = 0; o < co; ++o) {
+        float r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc = sB[o];
+#pragma unroll
+            for (int i = 0; i < CIMAX; ++i) acc = fmaf(sM[o][i], v[i][q], acc);
+            r[q] = acc;
+        }
+        const size_t oi = ((size_t)b * co + o) * npix + p;
+        if (pre) *reinterpret_cast<float4*>(pre + oi) = make_float4(r[0], r[1], r[2], r[3]);
+        if (act == FNO_ACT_GELU)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[q] = gelu(r[q]);
+        if constexpr (sizeof(Tout) == 4) {
+            *reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + oi) = make_float4(r[0], r[1], r[2], r[3]);
+        } else {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(r[0], r[1]), hi = __floats2bfloat162_rn(r[2], r[3]);
+            uint2 u;
+            u.x = *reinterpret_cast<const uint32_t*>(&lo);
+            u.y = *reinterpret_cast<const uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(out) + oi) = u;
+        }
+    }
+}
+
 // --- the same channel mix on the 5th-generation tensor cores (BF16 inference) -----------
 // One CTA (4 warps) computes 128-pixel pieces of rw consecutive rows (b, z) for
 // all co outputs, one row at a time, as
@@ -1245,6 +1309,15 @@ void combine_dispatch(int B, int ci, int co, int Nz, int Nx, int mx, const void*
                       const float* bias, const float* T, const float* tab, int act, float* pre, void* out,
                       cudaStream_t s)
 {
+    const long long npix = (long long)Nz * Nx;
+    const bool al16 = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
+                        reinterpret_cast<uintptr_t>(pre)) & 15) == 0;
+    if (!T && ci <= 4 && (npix & 3) == 0 && al16 && npix / 4 / 256 < 0x7fffffffLL) {
+        const dim3 grid((unsigned)((npix / 4 + 255) / 256), B);
+        k_combine_px4<4, Tin, Tout><<<grid, 256, 0, s>>>(ci, co, npix, static_cast<const Tin*>(in), M, mt, bias, act,
+                                                         pre, static_cast<Tout*>(out));
+        return;
+    }
     if (ci <= 4) combine_launch<4, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
     else if (ci <= 8) combine_launch<8, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
     else if (ci <= 16) combine_launch<16, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);

@@ -89,6 +89,23 @@ def test_fused_mix_and_inverse_z(B, Ci, Co, Nz, mz, mx):
     assert rel(fc[..., 0] + 1j * fc[..., 1], ref) < 1e-5
 
 
+@pytest.mark.parametrize("Nz,Nx,dtype", [(16, 36, torch.float32), (16, 36, torch.bfloat16), (7, 9, torch.float32)])
+def test_lift_path_matches_reference(Nz, Nx, dtype):
+    """fno_combine with few input channels and no spectral term (the lift; four
+    pixels per thread when Nz Nx is a multiple of 4, the general kernel otherwise):
+    pre-activation, GELU output and the transposed weight layout against FP64."""
+    B, ci, co = 2, 3, 32
+    x = RNG.standard_normal((B, ci, Nz, Nx))
+    M, b = RNG.standard_normal((co, ci)), RNG.standard_normal(co)
+    pre = torch.empty((B, co, Nz, Nx), dtype=torch.float32, device="cuda")
+    out = fno.fno_combine(dev(x), dev(M), co, bias=dev(b), act=fno.ACT_GELU, pre=pre, out_dtype=dtype)
+    ref = ofno.pointwise(M, b, x)
+    assert rel(pre.cpu().numpy(), ref) < 1e-6
+    assert rel(out.float().cpu().numpy(), ofno.gelu(ref)) < (1e-2 if dtype == torch.bfloat16 else 1e-6)
+    outt = fno.fno_combine(dev(x), dev(np.ascontiguousarray(M.T)), co, m_trans=True, bias=dev(b))
+    assert rel(outt.cpu().numpy(), ref) < 1e-6
+
+
 def test_mode_mix_and_backward():
     B, Ci, Co, KZ, mx = 3, 5, 7, 8, 6
     X = RNG.standard_normal((B, Ci, KZ, mx)) + 1j * RNG.standard_normal((B, Ci, KZ, mx))
