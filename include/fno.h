@@ -114,15 +114,18 @@ wave_status_t fno_combine(int B, int Ci, int Co, int Nz, int Nx, int mx, const v
 wave_status_t fno_project(int B, int Ci, int H, int Nz, int Nx, const void* in, int in_bf16, const float* Q1,
                           const float* q1, const float* Q2, const float* q2, float* out, void* stream);
 
-/* With the tensor cores allowed (fno_set_tensor_cores(1), the default), fno_combine runs
- * on them (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory)
- * when in and out are bf16, pre is NULL, m_trans = 0, Ci = 32 and Co is 32 or
- * 64 -- the BF16 inference path of the Fourier layers (and fno_project under
- * the conditions stated there); the weights, the table and the spectral coefficients are rounded
- * to BF16 on their way into shared memory.  fno_set_tensor_cores(0) keeps the
- * CUDA-core kernel everywhere.  fno_tensor_core_status synchronises the device,
- * returns WAVE_ERR_TIMEOUT if a tensor-core launch since the last call gave up
- * waiting for its MMAs (its results are then invalid), and clears the flag. */
+/* With the tensor cores allowed (fno_set_tensor_cores(1), the default), the BF16
+ * inference path runs on them (tcgen05.mma, BF16 operands, FP32 accumulation in
+ * tensor memory): fno_combine when in and out are bf16, pre is NULL, m_trans = 0,
+ * Ci = 32 and Co is 32 or 64; fno_project under the conditions stated there;
+ * fno_dft_x when in is bf16.  The weights, the tables and the spectral
+ * coefficients are rounded to BF16 on their way into shared memory, the bias to
+ * two BF16 parts (about 16 significant bits), and GELU there evaluates erf by
+ * Abramowitz and Stegun's formula 7.1.26 (|error| <= 1.5e-7).
+ * fno_set_tensor_cores(0) keeps the CUDA-core kernels everywhere.
+ * fno_tensor_core_status synchronises the device, returns WAVE_ERR_TIMEOUT if a
+ * tensor-core launch since the last call gave up waiting for its MMAs (its
+ * results are then invalid), and clears the flag. */
 wave_status_t fno_set_tensor_cores(int on);
 wave_status_t fno_tensor_core_status(void);
 

@@ -1,10 +1,14 @@
 // fno.cu -- kernels of the Fourier neural operator used as a learned
 // preconditioner: twiddle tables, the truncated DFT along x and z and their
-// inverse directions, the per-mode complex channel mix and its backward, the
-// fused pointwise channel mix + spectral inverse + GELU, weight gradients, the
-// MSE loss and the Adam update.  The operations and layouts are those of
-// include/fno.h; the network is the FNO of Li et al. (2020) that the paper
-// uses as a learned surrogate (section "Fourier neural operator surrogates").
+// inverse directions, the per-mode complex channel mix (alone, and fused with
+// the inverse z transform) and its backward, the fused pointwise channel mix +
+// spectral inverse + GELU, the fused projection head, weight gradients, the MSE
+// loss and the Adam update.  BF16 inference runs the channel mix, the
+// projection head and the x transform on the 5th-generation tensor cores
+// (tcgen05, operands in shared memory, accumulators in tensor memory).  The
+// operations and layouts are those of include/fno.h; the network is the FNO of
+// Li et al. (2020) that the paper uses as a learned surrogate (section "Fourier
+// neural operator surrogates").
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -791,7 +795,8 @@ __global__ void __launch_bounds__(128) k_combine_tc(int Nz, int Nx, int mx, int 
 // A[r][x] = in[r0 + r][x] and B[n][x] = table[x][n] (zero for n >= 2 mx), K = Nx
 // in chunks of 64 staged K-major (stride offset 1024 B between 8-row groups)
 // into two alternating buffers; the MMAs of a chunk are committed to that
-// buffer's mbarrier, which is waited on before the buffer is refilled.
+// buffer's mbarrier, which is waited on before the buffer is refilled.  Used
+// for rows whose length is not a multiple of 8 (k_dft_x_tc2 below otherwise).
 constexpr int kTcKc = 64;
 
 
