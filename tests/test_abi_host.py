@@ -42,6 +42,39 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def test_fno_entry_points_reject_bad_sizes_before_any_launch():
+    """Argument checks of the FNO calls run on the host: a size outside the
+    documented limits returns WAVE_ERR_ARG, and an empty batch returns WAVE_OK,
+    without touching the (fake, never dereferenced) device pointers."""
+    from paper_2304_05592_gb300 import fno
+
+    lib = fno._lib()
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    ARG, OK = 1, 0
+    # fno_project(B, Ci, H, Nz, Nx, in, in_bf16, Q1, q1, Q2, q2, out, stream)
+    assert lib.fno_project(-1, 32, 64, 8, 8, fake, 1, fake, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_project(2, 65, 64, 8, 8, fake, 1, fake, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_project(2, 32, 0, 8, 8, fake, 1, fake, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_project(2, 32, 64, 8, 8, fake, 1, None, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_project(0, 32, 64, 8, 8, fake, 1, fake, None, fake, None, fake, None) == OK
+    # fno_mix_idft_z(B, Ci, Co, Nz, mz, mx, X, R, tz, out, stream): mx <= 16, 2 mz <= Nz
+    assert lib.fno_mix_idft_z(2, 32, 32, 256, 16, 17, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_mix_idft_z(2, 32, 32, 30, 16, 16, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_mix_idft_z(2, 65, 32, 256, 16, 16, fake, fake, fake, fake, None) == ARG
+    assert lib.fno_mix_idft_z(0, 32, 32, 256, 16, 16, fake, fake, fake, fake, None) == OK
+    # fno_combine(B, Ci, Co, Nz, Nx, mx, in, in_bf16, M, m_trans, bias, T, table, act, pre, out, out_bf16, stream)
+    assert lib.fno_combine(2, 32, 65, 8, 8, 1, fake, 1, fake, 0, None, None, None, 0, None, fake, 1, None) == ARG
+    assert lib.fno_combine(2, 32, 32, 8, 8, 17, fake, 1, fake, 0, None, fake, fake, 0, None, fake, 1, None) == ARG
+    assert lib.fno_combine(2, 32, 32, 8, 8, 1, fake, 1, fake, 0, None, None, None, 7, None, fake, 1, None) == ARG
+    assert lib.fno_combine(0, 32, 32, 8, 8, 1, fake, 1, fake, 0, None, None, None, 1, None, fake, 1, None) == OK
+    # fno_dft_x(rows, Nx, mx, in, in_bf16, table, out, stream)
+    assert lib.fno_dft_x(10, 64, 0, fake, 1, fake, fake, None) == ARG
+    assert lib.fno_dft_x(0, 64, 16, fake, 1, fake, fake, None) == OK
+    assert lib.fno_set_tensor_cores(2) == ARG
+    assert lib.fno_wgrad_work_floats(-1, 32, 32, 100) == 0
+
+
 def test_courant_limit_matches_oracle():
     for nd in (2, 3):
         assert abs(wave.wave_courant_limit(nd) - oracle.courant_limit(nd)) < 1e-12
