@@ -215,13 +215,13 @@ def cpu_baseline(nt: int):
             "sample": f"1 shot of the 32 (full grid, nt={nt}), one gradient, FP64, {el:.1f} s"}
 
 
-def _variant3d():
-    """The 3D step variant the library runs by default (TMA plane ring, 8-row
-    tiles, 64 planes per CTA, 10 ring slots)."""
-    return "5 (k_step3d_tma<8,64,10>)"
+def _variant3d(v: int) -> str:
+    """Label of a 3D step variant; -1 is the library default, variant 5 (TMA plane
+    ring, 8-row tiles, 64 planes per CTA, 10 ring slots), whose traffic was captured."""
+    return "5 (k_step3d_tma<8,64,10>)" if v in (-1, 5) else str(v)
 
 
-def config3_forward(dev, peak, nt: int = 200):
+def config3_forward(dev, peak, nt: int = 200, variant: int = -1):
     """3D config-3 forward (400 x 400 x 300 at 10 m, 160 000 receivers), nt steps."""
     import torch
 
@@ -245,9 +245,10 @@ def config3_forward(dev, peak, nt: int = 200):
     ach = 16 * N / avg / 1e9
     return {"workload": "3D forward 400x400x300 at 10 m + 40-cell sponge (480x480x380 padded), 160000 receivers, "
                         f"{p.nt} of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
-            "kernel": f"3D step variant {wave.wave_variant_count(2) and _variant3d()}", "avg_launch_us": avg * 1e6,
+            "kernel": f"3D step variant {_variant3d(variant)}", "avg_launch_us": avg * 1e6,
             "achieved_gbs": ach, "frac": ach / peak,
-            "traffic": TRAFFIC.get(("k_step3d_tma<8,64,10,fwd>", kernel_hash("k_step3d_tma"))),
+            "traffic": TRAFFIC.get(("k_step3d_tma<8,64,10,fwd>", kernel_hash("k_step3d_tma")))
+            if variant in (-1, 5) else None,
             "bound": "hbm", "bytes_per_point": 16}
 
 
@@ -365,7 +366,7 @@ def main():
         from paper_2304_05592_gb300 import wave as _w
 
         _w.wave_set_variant(2, args.variant_3d)
-        print(json.dumps({"config3_forward": config3_forward(dev, hbm_peak()[0], args.only_3d)}))
+        print(json.dumps({"config3_forward": config3_forward(dev, hbm_peak()[0], args.only_3d, args.variant_3d)}))
         return 0
     from paper_2304_05592_gb300 import wave
     from paper_2304_05592_gb300.wave import Grid
