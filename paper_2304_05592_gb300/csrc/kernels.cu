@@ -578,6 +578,12 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
         fence_mbar_init();
     }
     __syncthreads();
+    // Programmatic dependent launch: the next step's CTAs may be scheduled once
+    // every CTA of this grid has started, and this grid touches global memory
+    // only after the previous kernel in the stream has finished and its writes
+    // are visible (both are no-ops for a launch without the attribute).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (tid == 0) {
         mbar_expect_tx(&bar[0], kBytes);
         tma_load_4d(st, mh, &bar[0], x0 - 4, z0 - 4, s0, a.u_buf);
@@ -1918,8 +1924,19 @@ static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStr
         cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, FL, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
-    dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
-    k_step2d_sgt<TZ, BZ, G, FL, ADJ><<<grid, dim3(32, BZ), smem, s>>>(*maps, a);
+    // launched with programmatic stream serialization: consecutive steps overlap the
+    // launch and set-up of one with the last CTAs of the other (see the kernel)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
+    cfg.blockDim = dim3(32, BZ);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_step2d_sgt<TZ, BZ, G, FL, ADJ>, *maps, a);
 }
 
 template <int TZ, int BZ, bool ADJ>
