@@ -41,10 +41,10 @@ VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,fwd>"),
                   (0, 27): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,fwd>"),
                   (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>"),
                   (1, 25): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,adj>")}
-TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "975aabe1792167d4"): 81.84e6,
-           ("k_step2d_sgt<16,8,2,1,fwd>", "975aabe1792167d4"): 81.89e6,
-           ("k_step2d_sgt<16,8,2,0,adj>", "975aabe1792167d4"): 93.86e6,
-           ("k_step2d_sgt<16,8,2,1,adj>", "975aabe1792167d4"): 94.70e6,
+TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "b1aa5bc1b5bee470"): 81.70e6,
+           ("k_step2d_sgt<16,8,2,1,fwd>", "b1aa5bc1b5bee470"): 81.73e6,
+           ("k_step2d_sgt<16,8,2,0,adj>", "b1aa5bc1b5bee470"): 93.41e6,
+           ("k_step2d_sgt<16,8,2,1,adj>", "b1aa5bc1b5bee470"): 93.96e6,
            ("k_step3d_tma<8,64,10,fwd>", "ff84bd7b5179962b"): 1434.45e6}
 
 
