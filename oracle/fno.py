@@ -88,6 +88,21 @@ def idft_trunc_adjoint(dy: np.ndarray, mz: int, mx: int) -> np.ndarray:
 
 # --- pointwise pieces ---------------------------------------------------------
 
+def twiddle_tables(Nz: int, Nx: int, mz: int, mx: int):
+    """The factors of the separable truncated transforms above, as complex
+    arrays: fwd[x, kx] = exp(-i 2 pi kx x / Nx) (the x part of T), inv[x, kx] =
+    w_kx / (Nz Nx) exp(+i 2 pi kx x / Nx) (the x part of S), bwd = conj(inv)
+    (the x part of S'), adj = conj(fwd) (the x part of T'), and the z factors
+    ez[z, a] = exp(+i 2 pi kz_a z / Nz) over the retained rows kz_a."""
+    x = np.arange(Nx)[:, None]
+    kx = np.arange(mx)[None, :]
+    fwd = np.exp(-2j * np.pi * kx * x / Nx)
+    w = np.where(kx == 0, 1.0, 2.0) / (Nz * Nx)
+    inv = w * np.conj(fwd)
+    ez = np.exp(2j * np.pi * np.arange(Nz)[:, None] * kz_rows(Nz, mz)[None, :] / Nz)
+    return fwd, inv, np.conj(inv), np.conj(fwd), ez
+
+
 def gelu(x):
     return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
 

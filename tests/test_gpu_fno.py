@@ -42,6 +42,16 @@ def pack(c):
     return dev(np.stack([c.real, c.imag], axis=-1))
 
 
+@pytest.mark.parametrize("Nz,Nx,mz,mx", [(24, 40, 4, 5), (256, 512, 16, 16), (37, 70, 3, 7)])
+def test_tables_match_oracle(Nz, Nx, mz, mx):
+    """fno_tables (double on the device, rounded to float) against the factors
+    of the truncated transforms computed from their definition."""
+    (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, mz, mx)
+    for got, ref in zip((tf, ti, tb, ta, tz), ofno.twiddle_tables(Nz, Nx, mz, mx)):
+        g = got.cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(g[..., 0] + 1j * g[..., 1], ref, rtol=0, atol=2e-7 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("shape", [(2, 3, 24, 40, 4, 5), (1, 32, 256, 512, 16, 16), (3, 2, 37, 70, 3, 7)])
 def test_truncated_dft_and_inverse(shape):
     B, C, Nz, Nx, mz, mx = shape
@@ -82,8 +92,7 @@ def test_fused_mix_and_inverse_z(B, Ci, Co, Nz, mz, mx):
     Xc = X[..., 0] + 1j * X[..., 1]
     Rc = R[..., 0] + 1j * R[..., 1]
     Yc = np.einsum("biam,ioam->boam", Xc, Rc)
-    E = tz.cpu().numpy().astype(np.float64)
-    Ec = E[..., 0] + 1j * E[..., 1]  # [Nz][KZ]
+    Ec = ofno.twiddle_tables(Nz, 2 * mx, mz, mx)[4]  # [Nz][KZ], from the definition
     ref = np.einsum("boam,za->bozm", Yc, Ec)
     fc = fused.reshape(B, Co, Nz, mx, 2)
     assert rel(fc[..., 0] + 1j * fc[..., 1], ref) < 1e-5
@@ -226,10 +235,11 @@ def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nz, 
     same BF16 activations, on row lengths that leave a ragged 128-pixel tile
     (some not a multiple of 4 or 8) and ragged groups of rows."""
     B, ci, mz = 2, 32, 4
-    x = torch.from_numpy(RNG.standard_normal((B, ci, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
+    x = torch.from_numpy(RNG.standard_normal((B, ci, Nz, Nx)).astype(np.float32)).to(torch.bfloat16).cuda()
     M, b = RNG.standard_normal((co, ci)) / np.sqrt(ci), RNG.standard_normal(co)
     (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, mz, mx)
-    T = dev(RNG.standard_normal((B * co, Nz, mx, 2)) * 50.0) if spectral else None
+    Th = RNG.standard_normal((B * co, Nz, mx, 2)) * 50.0
+    T = dev(Th) if spectral else None
     kw = dict(bias=dev(b), act=fno.ACT_GELU, out_dtype=torch.bfloat16)
     if spectral:
         kw.update(T=T, table=ti, mx=mx)
@@ -244,9 +254,9 @@ def test_tensor_core_combine_matches_cuda_cores_and_reference(co, spectral, Nz, 
     xf = x.float().cpu().numpy().astype(np.float64)
     pre = ofno.pointwise(M, b, xf)
     if spectral:
-        Tn = T.cpu().numpy().astype(np.float64).reshape(B, co, Nz, mx, 2)
-        tab = ti.cpu().numpy().astype(np.float64)
-        pre += Tn[..., 0] @ tab[..., 0].T - Tn[..., 1] @ tab[..., 1].T
+        Tn = Th.astype(np.float32).astype(np.float64).reshape(B, co, Nz, mx, 2)
+        inv = ofno.twiddle_tables(Nz, Nx, mz, mx)[1]  # [Nx][mx]
+        pre += Tn[..., 0] @ inv.real.T - Tn[..., 1] @ inv.imag.T
     ref = ofno.gelu(pre)
     # BF16 operands and output: relative errors of a few 1e-3
     assert rel(out_tc, ref) < 1e-2, rel(out_tc, ref)
@@ -262,7 +272,7 @@ def test_tensor_core_x_transform_matches_reference(shape):
     through the staged kernel) against the CUDA-core kernel and an FP64
     reference."""
     B, C, Nz, Nx, mx = shape
-    v = torch.from_numpy(RNG.standard_normal((B, C, Nz, Nx)).astype(np.float32)).cuda().to(torch.bfloat16)
+    v = torch.from_numpy(RNG.standard_normal((B, C, Nz, Nx)).astype(np.float32)).to(torch.bfloat16).cuda()
     (tf, ti, tb, ta), tz = fno.fno_tables(Nz, Nx, 4, mx)
     try:
         fno.fno_set_tensor_cores(True)
@@ -273,8 +283,8 @@ def test_tensor_core_x_transform_matches_reference(shape):
     finally:
         fno.fno_set_tensor_cores(True)
     vf = v.float().cpu().numpy().astype(np.float64).reshape(-1, Nx)
-    tab = tf.cpu().numpy().astype(np.float64).reshape(Nx, 2 * mx)
-    ref = vf @ tab
+    fwd = ofno.twiddle_tables(Nz, Nx, 4, mx)[0]  # [Nx][mx]
+    ref = (vf @ fwd).view(np.float64)  # interleaved (re, im) per mode
     assert rel(out_tc.reshape(ref.shape), ref) < 1e-2
     assert rel(out_cc.reshape(ref.shape), ref) < 1e-5
 

@@ -70,30 +70,56 @@ def test_config2_batched_gradient_is_the_sum_of_shot_gradients(config2):
     assert abs(config2["phi"] - phis) <= 1e-6 * phis
 
 
-def test_config2_gradient_of_sampled_shots_matches_oracle(config2):
+@pytest.fixture(scope="module")
+def config2_oracle(config2):
+    """Observed data of two sampled shots modelled by the oracle on the true
+    model, and the oracle's misfit and gradient of each at the starting model."""
     p, v0, q1 = config2["p"], config2["v0"], config2["q1"]
-    dev = torch.device("cuda")
-    g = Grid.of(p)
-    vel = torch.from_numpy(v0).to(dev)
+    out = {}
     for s in (5, 26):
-        d_obs = config2["d_obs"][s:s + 1].contiguous()
-        phi, gs, _ = wave.wave_gradient(g, vel, p.src[s:s + 1], config2["wav"][s:s + 1], p.rec[s:s + 1], d_obs,
-                                        nsnap=256)
-        phi_r, g_r = oracle.gradient(ogrid(p), v0, p.src[s:s + 1], q1[None, :, None], p.rec[s:s + 1],
-                                     d_obs.cpu().numpy())
+        d_obs = oracle.forward(ogrid(p), p.vel, p.src[s:s + 1], q1[None, :, None], p.rec[s:s + 1])
+        phi_r, g_r = oracle.gradient(ogrid(p), v0, p.src[s:s + 1], q1[None, :, None], p.rec[s:s + 1], d_obs)
+        out[s] = (d_obs, phi_r, g_r)
+    return out
+
+
+def _shot_gradient(config2, s, d_obs, store):
+    p = config2["p"]
+    dev = torch.device("cuda")
+    vel = torch.from_numpy(config2["v0"]).to(dev)
+    dd = torch.from_numpy(d_obs.astype(np.float32)).to(dev)
+    return wave.wave_gradient(Grid.of(p), vel, p.src[s:s + 1], config2["wav"][s:s + 1], p.rec[s:s + 1], dd,
+                              store=store, nsnap=256)
+
+
+def test_config2_gradient_of_sampled_shots_matches_oracle(config2, config2_oracle):
+    for s, (d_obs, phi_r, g_r) in config2_oracle.items():
+        phi, gs, _ = _shot_gradient(config2, s, d_obs, wave.STORE_CHECKPOINT)
         assert abs(phi - phi_r) <= 1e-4 * phi_r
         assert rel(gs.cpu().numpy(), g_r) < 1e-3, (s, rel(gs.cpu().numpy(), g_r))
 
 
-def test_config2_bf16_store_error_is_stated(config2):
-    """The BF16 wavefield store changes the gradient by a stated amount (the
-    stencil and accumulation stay FP32); it must stay below 1e-2 relative."""
+def test_config2_bf16_store_error_is_stated(config2, config2_oracle):
+    """The BF16 wavefield store (stencil arithmetic and accumulation stay FP32)
+    changes the gradient by a stated amount: against the FP64 oracle on two
+    sampled shots of the benchmark survey, and against the FP32 checkpointed
+    gradient of the whole 32-shot batch.  Both must stay below 1e-2."""
+    errs = {}
+    for s, (d_obs, phi_r, g_r) in config2_oracle.items():
+        phi, g16, _ = _shot_gradient(config2, s, d_obs, wave.STORE_BF16)
+        _, g32, _ = _shot_gradient(config2, s, d_obs, wave.STORE_CHECKPOINT)
+        errs[s] = (rel(g16.cpu().numpy(), g_r), rel(g32.cpu().numpy(), g_r))
+        assert abs(phi - phi_r) <= 1e-4 * phi_r
+    for s, (e16, e32) in errs.items():
+        print(f"config 2 shot {s}: gradient rel L2 vs FP64 oracle: BF16 store {e16:.3e}, "
+              f"FP32 checkpointed {e32:.3e}")
+    assert max(e for e, _ in errs.values()) < 1e-2
     p = config2["p"]
     dev = torch.device("cuda")
     _, g16, _ = wave.wave_gradient(Grid.of(p), torch.from_numpy(config2["v0"]).to(dev), p.src, config2["wav"],
                                    p.rec, config2["d_obs"], store=wave.STORE_BF16)
     e = rel(g16.cpu().numpy(), config2["grad"].astype(np.float64))
-    print(f"BF16 store vs FP32 checkpointed gradient: rel L2 {e:.3e}")
+    print(f"config 2, 32 shots: BF16 store vs FP32 checkpointed gradient: rel L2 {e:.3e}")
     assert e < 1e-2
 
 

@@ -2,7 +2,8 @@
 wavelet and the band-limited noise match the FP64 oracle; the vector updates
 are exact; stochastic FWI with four random shots per iteration lowers the
 misfit over all shots on low-cut, noisy data; the time-lapse batch (all vintage x shot
-pairs in one uneven batch) equals one gradient call per vintage."""
+pairs in one uneven batch) matches the FP64 oracle vintage by vintage and equals one
+gradient call per vintage."""
 import numpy as np
 import pytest
 import torch
@@ -31,9 +32,11 @@ def dev(a):
 
 @pytest.mark.parametrize("nt,dt", [(2000, 0.8e-3), (1001, 0.5e-3)])
 def test_lowcut_matches_oracle(nt, dt):
-    q = wave.wave_ricker(15.0, dt, nt)
-    y = wave.wave_lowcut(q, dt, 4.0, 6.0).cpu().numpy()
-    ref = oc.lowcut(q.cpu().numpy().astype(np.float64), dt, 4.0, 6.0)
+    import oracle
+
+    qh = oracle.ricker(15.0, dt, nt).astype(np.float32)
+    y = wave.wave_lowcut(dev(qh), dt, 4.0, 6.0).cpu().numpy()
+    ref = oc.lowcut(qh.astype(np.float64), dt, 4.0, 6.0)
     assert rel(y, ref) < 1e-6
     f = np.arange(nt // 2 + 1) / (nt * dt)
     Y = np.abs(np.fft.rfft(y.astype(np.float64)))
@@ -44,11 +47,12 @@ def test_noise_matches_oracle_and_snr():
     rng = np.random.default_rng(5)
     data = rng.standard_normal((3, 400, 37)).astype(np.float32)
     white = rng.standard_normal(data.shape).astype(np.float32)
-    q = wave.wave_ricker(15.0, 0.8e-3, 200)
-    filt = wave.wave_lowcut(q, 0.8e-3, 4.0, 6.0)
-    center = int(torch.argmax(filt.abs()).item())
-    out = wave.wave_add_noise(dev(data), dev(white), filt, center, 10.0).cpu().numpy()
-    ref = oc.add_noise(data, white, filt.cpu().numpy(), center, 10.0)
+    import oracle
+
+    filt = oc.lowcut(oracle.ricker(15.0, 0.8e-3, 200), 0.8e-3, 4.0, 6.0).astype(np.float32)
+    center = int(np.argmax(np.abs(filt)))
+    out = wave.wave_add_noise(dev(data), dev(white), dev(filt), center, 10.0).cpu().numpy()
+    ref = oc.add_noise(data, white, filt, center, 10.0)
     assert rel(out, ref) < 1e-5
     noise = out.astype(np.float64) - data
     assert abs(20 * np.log10(np.linalg.norm(data) / np.linalg.norm(noise)) - 10.0) < 1e-3
@@ -89,6 +93,33 @@ def test_stochastic_fwi_with_lowcut_noisy_data_reduces_full_misfit():
     assert last < 0.9 * first, h.full_misfit
     # most subset steps found descent
     assert sum(1 for a in h.step if a > 0) >= 6, h.step
+
+
+@pytest.mark.parametrize("store,tol", [(wave.STORE_FP32, 1e-3), (wave.STORE_BF16, 1e-2)])
+def test_timelapse_batch_matches_oracle_per_vintage(store, tol):
+    # the block-diagonal time-lapse operator: every (vintage, shot) pair in one uneven batch, each
+    # vintage's misfit and gradient checked against the FP64 oracle on its own model and data
+    import oracle
+
+    p, base, dv = _survey(nshot=3, nt=400)
+    acq = precond.Acquisition.of(p)
+    vints = [base, base + 0.5 * dv, base + dv]
+    models = [dev(v) for v in vints]
+    og = oracle.Grid(2, p.nx, p.nz, p.h, p.dt, p.nt, p.nb, vref=p.vref)
+    q32 = np.repeat(oracle.ricker(p.f0, p.dt, p.nt).astype(np.float32)[None, :, None], p.nshot, axis=0)
+    q = q32.astype(np.float64)  # the same wavelet values on both sides, from the oracle
+    d_obs_h = [oracle.forward(og, v.astype(np.float64), p.src, q, p.rec) for v in
+               (base + 0.1 * dv, base + 0.6 * dv, base + 1.1 * dv)]
+    d_obs = [dev(d) for d in d_obs_h]
+    mb, gb = fwi.timelapse_gradients(acq.grid, models, p.src, p.rec, dev(q32), d_obs, store=store,
+                                     wrt=wave.WRT_SLOWNESS2, batched=True)
+    errs = []
+    for i, v in enumerate(vints):
+        phi_ref, g_ref = oracle.gradient(og, v.astype(np.float64), p.src, q, p.rec, d_obs_h[i])
+        assert abs(mb[i] - phi_ref) <= 1e-4 * phi_ref, (i, mb[i], phi_ref)
+        errs.append(rel(gb[i].cpu().numpy(), g_ref))
+    print(f"time-lapse batch vs oracle, store {store}: gradient rel L2 per vintage {errs}")
+    assert max(errs) < tol, errs
 
 
 def test_timelapse_batch_equals_one_call_per_vintage():

@@ -143,3 +143,52 @@ def test_adam_first_step_is_sign_times_lr():
     # with m0 = v0 = 0 the bias-corrected first step is lr * g / (|g| + eps)
     p, m, v = fno.adam(np.array([1.0, -2.0]), np.array([0.5, -3.0]), np.zeros(2), np.zeros(2), 1, 0.1)
     np.testing.assert_allclose(p, [1.0 - 0.1 * 0.5 / (0.5 + 1e-8), -2.0 + 0.1 * 3.0 / (3.0 + 1e-8)], atol=1e-15)
+
+
+def test_adam_constant_gradient_moves_lr_per_step_for_every_t():
+    # with a constant gradient the bias-corrected moments are exactly g and g^2 at every t
+    # (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so each of the first steps moves
+    # lr * g / (|g| + eps); a bias-correction exponent frozen at 1 fails from t = 2 on
+    for b1, b2 in [(0.9, 0.999), (0.8, 0.95)]:
+        g = np.array([0.5, -3.0, 1e-8])
+        p, m, v = np.array([1.0, -2.0, 0.0]), np.zeros(3), np.zeros(3)
+        for t in range(1, 6):
+            p, m, v = fno.adam(p, g, m, v, t, 0.1, b1, b2)
+            np.testing.assert_allclose(m, (1 - b1 ** t) * g, rtol=1e-13, atol=0)
+            np.testing.assert_allclose(v, (1 - b2 ** t) * g * g, rtol=1e-13, atol=0)
+            step = 0.1 * g / (np.abs(g) + 1e-8)  # eps outside the square root: the tiny entry moves lr / 2
+            np.testing.assert_allclose(p, np.array([1.0, -2.0, 0.0]) - t * step, rtol=1e-12, atol=1e-15)
+
+
+def test_adam_alternating_gradient_matches_closed_form_moments():
+    # g_t = (-1)^(t+1): m_t = (1-b1) (-1)^(t+1) (1 - (-b1)^t) / (1 + b1) and v_t = 1 - b2^t, so
+    # vhat_t = 1 and the step is lr * m_t / (1 - b1^t) / (1 + eps); swapping b1 and b2 in the
+    # moment updates (or in the bias corrections) changes every one of these
+    lr = 0.05
+    for b1, b2 in [(0.9, 0.999), (0.8, 0.95)]:
+        p, m, v = np.array([0.3]), np.zeros(1), np.zeros(1)
+        expect_p = 0.3
+        for t in range(1, 8):
+            g = np.array([(-1.0) ** (t + 1)])
+            p, m, v = fno.adam(p, g, m, v, t, lr, b1, b2)
+            mt = (1 - b1) * (-1.0) ** (t + 1) * (1 - (-b1) ** t) / (1 + b1)
+            vt = 1 - b2 ** t
+            np.testing.assert_allclose(m, [mt], rtol=1e-13)
+            np.testing.assert_allclose(v, [vt], rtol=1e-13)
+            expect_p -= lr * (mt / (1 - b1 ** t)) / (1.0 + 1e-8)
+            np.testing.assert_allclose(p, [expect_p], rtol=1e-13)
+
+
+def test_twiddle_tables_factor_the_truncated_transforms():
+    # T v = sum_z conj(ez) (v fwd), S Y = Re(ez Y inv^T), and the two adjoints through bwd and adj,
+    # against the brute-force-pinned dft_trunc / idft_trunc and their adjoints
+    rng = np.random.default_rng(11)
+    Nz, Nx, mz, mx = 10, 14, 3, 4
+    fwd, inv, bwd, adj, ez = fno.twiddle_tables(Nz, Nx, mz, mx)
+    v = rng.standard_normal((Nz, Nx))
+    np.testing.assert_allclose(np.conj(ez).T @ (v @ fwd), fno.dft_trunc(v, mz, mx), atol=1e-11)
+    Y = rng.standard_normal((2 * mz, mx)) + 1j * rng.standard_normal((2 * mz, mx))
+    np.testing.assert_allclose(((ez @ Y) @ inv.T).real, fno.idft_trunc(Y, Nz, Nx), atol=1e-13)
+    dy = rng.standard_normal((Nz, Nx))
+    np.testing.assert_allclose(np.conj(ez).T @ (dy @ bwd), fno.idft_trunc_adjoint(dy, mz, mx), atol=1e-13)
+    np.testing.assert_allclose(((ez @ Y) @ adj.T).real, fno.dft_trunc_adjoint(Y, Nz, Nx), atol=1e-11)
