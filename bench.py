@@ -66,6 +66,13 @@ def parse():
     ap.add_argument("--variant-3d", type=int, default=-1, help="3D kernel variant (-1: library default)")
     ap.add_argument("--only-fno", action="store_true",
                     help="run only the FNO training/inference measurement and print its line (for profiling)")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the config-4 uneven batch and print its line (for profiling)")
+    ap.add_argument("--batch-nshot", type=int, default=64, help="problems in the uneven batch")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="grid and nt scale of the uneven batch (1 = config 4; smaller for profiling)")
+    ap.add_argument("--batch-quick", action="store_true",
+                    help="uneven batch: only the BF16 batched call (for profiling)")
     return ap.parse_args()
 
 
@@ -301,15 +308,19 @@ def fno_preconditioner(dev):
                                  "frac": ach / alu_peak, "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}}
 
 
-def uneven_batch(dev):
-    """Config 4: 64 shots of different grids, models and nt; one batched call
-    (persistent sweeps, CUDA graph, BF16 store) against one call per shot."""
+def uneven_batch(dev, nshot: int = 64, scale: float = 1.0, full: bool = True):
+    """Config 4: 64 shots of different grids, models and nt.  The batched
+    gradient (two persistent sweeps under a CUDA graph, sweep kernel chosen by
+    wave_autotune_batch on this batch) is timed directly with the BF16 store,
+    through the torch.autograd.Function (BatchMisfit: misfits forward,
+    velocity gradients backward) with the BF16 and the FP32 store, and against
+    one wave_gradient call per shot with autotuned step kernels."""
     import torch
 
-    from paper_2304_05592_gb300 import synth, wave
+    from paper_2304_05592_gb300 import autograd, synth, wave
     from paper_2304_05592_gb300.wave import BatchProblem, Grid
 
-    probs = synth.uneven_batch(seed=4, nshot=64)
+    probs = synth.uneven_batch(seed=4, nshot=nshot, scale=scale)
     bps = []
     pts = 0
     for pb in probs:
@@ -319,26 +330,61 @@ def uneven_batch(dev):
         dob = wave.wave_forward(g, v, pb.src, q[None].contiguous(), pb.rec)[0].contiguous()
         bps.append(BatchProblem(g, (v * 1.02).contiguous(), pb.src[0], q, pb.rec[0], dob))
         pts += 2 * (pb.nt - 1) * pb.padded_points
-    ws = wave.wave_workspace_size_batch(bps)
-    work = torch.empty(ws, dtype=torch.uint8, device=dev)
-    wave.wave_gradient_batch(bps, work=work)  # captures the graph
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    wave.wave_gradient_batch(bps, work=work)
-    torch.cuda.synchronize()
-    el_b = time.perf_counter() - t
-    del work
-    torch.cuda.empty_cache()
-    t = time.perf_counter()
-    for bp in bps:
-        wave.wave_gradient(bp.grid, bp.vel, bp.src[None], bp.wavelet[None].contiguous(), bp.rec[None],
-                           bp.d_obs[None].contiguous(), store=wave.STORE_BF16)
-    torch.cuda.synchronize()
-    el_p = time.perf_counter() - t
-    return {"workload": "64 2D shots, nx 256-768, nz 128-384, h 6.25-12.5 m, nt 1500-4000, layered models, "
-                        "BF16 store", "shot_gradients_per_s_batched": len(bps) / el_b,
-            "shot_gradients_per_s_one_call_per_shot": len(bps) / el_p, "pt_updates_per_s_batched": pts / el_b,
-            "workspace_gb": ws / 1e9, "batched": "2 persistent sweeps in a CUDA graph"}
+    out = {"workload": "64 2D shots, nx 256-768, nz 128-384, h 6.25-12.5 m, nt 1500-4000, layered models"
+           if nshot == 64 and scale == 1.0 else f"{nshot} 2D shots of the config-4 recipe scaled by {scale}",
+           "batched": "2 persistent sweeps in a CUDA graph"}
+
+    def timed(fn):
+        fn()  # first call: set-up, graph capture
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t
+
+    for store, name in ((wave.STORE_BF16, "bf16"), (wave.STORE_FP32, "fp32")):
+        if store == wave.STORE_FP32 and not full:
+            continue
+        ws = wave.wave_workspace_size_batch(bps, store)
+        work = torch.empty(ws, dtype=torch.uint8, device=dev)
+        vf, va = wave.wave_autotune_batch(bps, store=store, steps=200, work=work)
+        grads = [torch.empty(b.grid.phys_shape, dtype=torch.float32, device=dev) for b in bps]
+        el = timed(lambda: wave.wave_gradient_batch(bps, store=store, grads=grads, work=work))
+        del work
+        torch.cuda.empty_cache()
+        vels = [b.vel.requires_grad_(True) for b in bps]
+
+        def via_autograd():
+            m = autograd.batch_misfit(bps, store=store)
+            m.sum().backward()
+            for v in vels:
+                v.grad = None
+
+        el_ag = timed(via_autograd) if full else None
+        for b in bps:
+            b.vel.requires_grad_(False)
+        torch.cuda.empty_cache()
+        out[name] = {"shot_gradients_per_s_batched": len(bps) / el, "pt_updates_per_s_batched": pts / el,
+                     "shot_gradients_per_s_autograd": len(bps) / el_ag if el_ag else None,
+                     "sweep_variants": {"forward": vf, "adjoint": va, "chosen_by": "wave_autotune_batch"},
+                     "workspace_gb": ws / 1e9}
+    if full:
+        # one call per shot, each shape's step kernels autotuned first (BF16 store, as the batched line)
+        for bp in bps:
+            wave.wave_autotune(bp.grid, bp.vel, bp.src[None], bp.wavelet[None].contiguous(), bp.rec[None], steps=10)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for bp in bps:
+            wave.wave_gradient(bp.grid, bp.vel, bp.src[None], bp.wavelet[None].contiguous(), bp.rec[None],
+                               bp.d_obs[None].contiguous(), store=wave.STORE_BF16)
+        torch.cuda.synchronize()
+        out["shot_gradients_per_s_one_call_per_shot"] = len(bps) / (time.perf_counter() - t)
+        out["one_call_per_shot"] = "wave_gradient per problem, BF16 store, step kernels from wave_autotune per shape"
+    # bytes of the sweeps at the BF16 store: 18 B per forward update, 26 B per adjoint update
+    b16 = out["bf16"]
+    half = b16["pt_updates_per_s_batched"] / 2
+    b16["achieved_gbs_at_22_b_per_update"] = half * (18 + 26) / 1e9
+    return out
 
 
 def main():
@@ -361,6 +407,10 @@ def main():
     __graft_entry__.build()
     if args.only_fno:
         print(json.dumps({"fno_preconditioner": fno_preconditioner(dev)}))
+        return 0
+    if args.only_batch:
+        print(json.dumps({"uneven_batch": uneven_batch(dev, args.batch_nshot, args.batch_scale,
+                                                       full=not args.batch_quick)}))
         return 0
     if args.only_3d:
         from paper_2304_05592_gb300 import wave as _w

@@ -7,7 +7,8 @@
  * learning"), section "Wave-equation-based inversion":
  *   F(m) = P_r A(m)^{-1} P_s^T           (Eq. eq-fwi), m = squared slowness,
  *   Phi(m) = 1/2 || F(m) q - d ||_2^2     (Eq. eq-fwi, the loss of the AD example),
- *   grad Phi = J'(F(m) q - d)             (judiJacobian, "gradient w.r.t. squared slowness"),
+ *   grad Phi = J'(F(m) q - d)             (judiJacobian; the paper's gradient is taken
+ *                                          with respect to the squared slowness),
  *   F' dy                                 (pullback of the rrule for F*q).
  * The paper leaves the discretisation open.  This library uses
  *   (M+E) u^{n+1} = (2M + dt^2 L) u^n - (M-E) u^{n-1} + dt^2 S q^n,  u^{-1} = u^0 = 0,
@@ -27,17 +28,24 @@
  *  - "dev" pointers are CUDA device memory, "host" pointers are host memory.
  *    The caller owns every buffer.  The library allocates nothing: all scratch
  *    comes from the caller's workspace (size from wave_workspace_size).
- *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is queued
- *    on that stream; every call synchronises the stream once after its set-up
- *    kernels (to validate the model against the stability limit before the
- *    time loop) and once at its end (to read the device error word), so a call
- *    returns with its results complete.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  wave_forward,
+ *    wave_adjoint, wave_gradient, wave_jacobian_adjoint and wave_born are
+ *    stream-ordered and asynchronous: they queue their work on the stream and
+ *    return without waiting for it (the set-up tables go through a pinned
+ *    host staging buffer of the library, so no copy waits either).  Results
+ *    are complete once the stream has reached the end of the call.
+ *  - Errors found before any launch (arguments, geometry, workspace size)
+ *    are returned by the call itself, without touching the outputs.
+ *    Errors found on the device -- a velocity that is not finite and
+ *    positive or a non-finite result (WAVE_ERR_NONFINITE), a time step above
+ *    the stability limit (WAVE_ERR_CFL), a bounded wait that gave up
+ *    (WAVE_ERR_TIMEOUT) -- set bits of an error word kept at the start of the
+ *    workspace; wave_status_wait(work, stream, ...) waits for the stream and
+ *    returns them.  Each call clears that word when it starts on the device,
+ *    so wave_status_wait reports the last call queued on the workspace.  When
+ *    it reports an error, the outputs of that call hold unspecified values.
  *  - Shot s uses sources src_xyz[s][0..nsrc) and receivers rec_xyz[s][0..nrec);
  *    every shot shares the grid and the velocity model.
- *  - Errors found before any launch (arguments, geometry, workspace size)
- *    return without touching the outputs.  WAVE_ERR_CFL and
- *    WAVE_ERR_NONFINITE are found after the set-up kernels and also leave the
- *    outputs untouched.
  */
 #ifndef WAVE_H
 #define WAVE_H
@@ -91,6 +99,15 @@ wave_status_t wave_workspace_size(const wave_grid_t* grid, int op, int nshot, in
                                   int nrec, const float* rec_xyz, int store, int nsnap,
                                   size_t* bytes /* host out */);
 
+/* Waits for `stream` and returns the device-side status of the last call
+ * queued on the workspace `work` (dev, as passed to that call): WAVE_OK,
+ * WAVE_ERR_CFL, WAVE_ERR_NONFINITE or WAVE_ERR_TIMEOUT from the error word,
+ * WAVE_ERR_CUDA if the stream reports a CUDA error (a failed kernel).
+ * misfit (host out, may be NULL) receives that call's misfit (wave_gradient;
+ * 0 for the other calls).  WAVE_ERR_ARG for a NULL workspace.  Not part of the
+ * paper: the status channel of the asynchronous calls. */
+wave_status_t wave_status_wait(const void* work, void* stream, double* misfit);
+
 /* Forward modelling d = F(m) q (Eq. eq-fwi, P_r A(m)^{-1} P_s^T).
  *   vel      dev  [nz][(ny)][nx] velocity (m/s)
  *   src_xyz  host [nshot][nsrc][ndim] source coordinates
@@ -126,7 +143,10 @@ typedef enum {
  *   d_obs    dev  [nshot][nt][nrec] observed data
  *   grad     dev  out [nz][(ny)][nx] dPhi/dm
  *   d_syn    dev  out [nshot][nt][nrec] synthetic data, or NULL
- *   misfit   host out Phi (double), or NULL
+ *   misfit   host out Phi (double), or NULL: written by a stream-ordered copy,
+ *            valid once the stream has reached the end of the call (pinned
+ *            memory keeps the call asynchronous; a pageable address makes the
+ *            call wait for its own work).  wave_status_wait also returns it.
  *   store    a wave_store_t; nsnap = checkpoint slots (CHECKPOINT only, >= 1)
  *   wrt      a wave_wrt_t: gradient w.r.t. m (default) or w.r.t. v */
 wave_status_t wave_gradient(const wave_grid_t* grid, const float* vel, int nshot, int nsrc,
@@ -161,14 +181,18 @@ wave_status_t wave_born(const wave_grid_t* grid, const float* vel, int nshot, in
  * application has reserved all device memory up front, or a latency-critical
  * loop that must not pay for an allocation and the synchronisation it can
  * bring.  The paper has no counterpart; this is a deployment convenience.
- * Same arguments, results and errors as wave_forward, minus work/work_bytes.
+ * Same arguments and results as wave_forward, minus work/work_bytes; unlike
+ * wave_forward it waits for its work and returns the device-side errors
+ * itself (the caller has no workspace to hand to wave_status_wait).
  * Scratch is a file-scope device array of WAVE_STATIC_WORKSPACE_BYTES inside
  * the library, held by every GPU that loads the library until the process
  * exits.  Problems whose workspace (wave_workspace_size, op 0) exceeds it
  * return WAVE_ERR_WORKSPACE before any device work.  The call allocates
- * nothing on the device.  The first call on a device looks up the array's
- * device address on that device (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call on a device shares the one array and
+ * nothing on the device.  Every call looks up the array's device address on
+ * the current device (cudaGetSymbolAddress), so a device reset between calls
+ * does no harm; the first call on a device may load the library's device code
+ * there, so make that first call before any stream capture.  Every call on a
+ * device shares the one array and
  * the array keeps the last call's contents (each call clears what must start
  * at zero): calls that overlap on the GPU, from two streams or two host
  * threads, race and must be serialised by the caller. */
@@ -192,8 +216,8 @@ typedef struct {
     double misfit;         /* out: 1/2 ||F q - d_obs||^2 of this problem    */
 } wave_problem_t;
 
-/* Low-cut wavelet for the paper's FWI experiment ("Ricker wavelet with no
- * energy below 4Hz", section "Deep priors and normalizing flows"): the real
+/* Low-cut wavelet for the paper's FWI experiment (a Ricker wavelet stripped of
+ * its content under 4 Hz, section "Deep priors and normalizing flows"): the real
  * DFT of q (nt samples, spacing dt) is multiplied by H(f) = 0 below f_cut, the
  * raised-cosine ramp 0.5 (1 - cos(pi (f - f_cut) / (f_pass - f_cut))) up to
  * f_pass and 1 above (f_k = k / (nt dt), k = 0..nt/2), and transformed back.
@@ -241,17 +265,41 @@ wave_status_t wave_workspace_size_batch(const wave_problem_t* probs, int nprob, 
  * axes and models (each problem is the gradient of wave_gradient for its own
  * single shot), computed together: one persistent forward sweep that stores
  * every level (store = WAVE_STORE_BF16 or WAVE_STORE_FP32) and one persistent
- * adjoint sweep, in which each 128 x 32 tile advances as soon as its
+ * adjoint sweep, in which each 128 x TZ tile advances as soon as its
  * neighbours have finished the previous step (bounded waits; a wait that
  * runs out returns WAVE_ERR_TIMEOUT).  The time loop has no per-step launch
- * and no global barrier, so short problems leave the sweep early.  With
- * use_graph != 0 the device work after the set-up is captured once into a
- * CUDA graph and replayed by later calls with the same problems and buffers.
- * Each problem's misfit field is written on return.  The batch is the
- * paper's per-shot parallelism of the gradient (section "Putting it all
- * together": gradients of randomly drawn shots per iteration). */
+ * and no global barrier, so short problems leave the sweep early.  The sweep
+ * kernel (tile height TZ, warps, pipeline depth, CTAs per SM) is the one
+ * wave_autotune_batch picked for batches of the same shapes, else a default.
+ * With use_graph != 0 the device work after the set-up is captured once into
+ * a CUDA graph and replayed by later calls with the same problems, buffers
+ * and kernel choice.  Each problem's misfit field is written on return (the
+ * call synchronises the stream).  The batch is the paper's per-shot
+ * parallelism of the gradient (section "Putting it all together": gradients
+ * of randomly drawn shots per iteration). */
 wave_status_t wave_gradient_batch(wave_problem_t* probs, int nprob, int store, int wrt, int use_graph, void* work,
                                   size_t work_bytes, void* stream);
+
+/* Autotuner of the uneven batch (no counterpart in the paper): runs the first
+ * `steps` steps of both sweeps of every sweep-kernel variant on this batch
+ * (same arguments and workspace as wave_gradient_batch; grads are not
+ * written), times them with CUDA events on `stream`, and records the fastest
+ * forward/adjoint pair with a common tile height for the batch's shapes
+ * (grid sizes, nb, nt, source and receiver counts, store); later
+ * wave_gradient_batch calls on batches of those shapes use it.  best_fwd /
+ * best_adj (host out, may be NULL) receive the chosen variants, numbered
+ * 0 .. wave_batch_variant_count() - 1.  Synchronises the stream. */
+wave_status_t wave_autotune_batch(wave_problem_t* probs, int nprob, int store, int steps, void* work,
+                                  size_t work_bytes, void* stream, int* best_fwd, int* best_adj);
+int wave_batch_variant_count(void);
+
+/* Forces the sweep kernels of later wave_gradient_batch calls (for tests and
+ * measurements; no counterpart in the paper): fwd and adj in
+ * [0, wave_batch_variant_count()) with the same tile height (variant 0: direct
+ * loads, 128 x 32 tiles; 1 and up: TMA producer/consumer sweeps), or both -1
+ * to return to the autotuned or default choice.  Process-wide; WAVE_ERR_ARG
+ * for an invalid pair. */
+wave_status_t wave_set_batch_variant(int fwd, int adj);
 
 /* Ricker wavelet q(t_n) = (1 - 2 a) exp(-a), a = (pi f0 (n dt - 1/f0))^2,
  * n = 0..nt-1 (the wavelet of the paper's FWI example, peak delayed by 1/f0).

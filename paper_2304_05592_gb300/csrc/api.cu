@@ -45,6 +45,15 @@ struct DevTaps {
 //   Born     : W0 W1 W2 (background levels) A0 A1 (scattered levels)
 // W = forward levels, A = adjoint levels, G = per-shot gradient accumulators,
 // Z = a zero batch (the state before the first step), S(k) = checkpoint slot k.
+// The first 256 bytes of every workspace: the device error word of the last
+// call queued on it and that call's misfit, read back by wave_status_wait.
+struct WsHeader {
+    int err[4];
+    double misfit;
+    float vmax;
+};
+static_assert(sizeof(WsHeader) <= 256, "the header fits the first carved block");
+
 struct Layout {
     Dims d;
     Tiling t;
@@ -165,10 +174,11 @@ wave_status_t plan(const wave_grid_t* g, int op, int nshot, int nsrc, const floa
         }
     }
     Carver c(base);
-    L.err = c.take<int>(4);
-    L.vmax = c.take<float>(1);
+    WsHeader* hdr = c.take<WsHeader>(1);  // offset 0
+    L.err = hdr ? hdr->err : nullptr;
+    L.vmax = hdr ? &hdr->vmax : nullptr;
+    L.misfit = hdr ? &hdr->misfit : nullptr;
     L.part = c.take<double>(kNumPartials);
-    L.misfit = c.take<double>(1);
     L.kap = c.take<float>(d.cell);
     carve_taps(c, L.hs, ncells_all, L.ts);
     carve_taps(c, L.hr, ncells_all, L.tr);
@@ -273,19 +283,130 @@ wave_status_t make_maps(Layout& L)
 
 // --- set-up ----------------------------------------------------------------
 
-wave_status_t upload_taps(const HostTaps& h, DevTaps& t, cudaStream_t s)
+// Pinned host staging for the set-up tables.  A copy from pageable host
+// memory makes the host wait for the stream's earlier work, so each call
+// instead writes its tables into a pinned buffer and uploads them with one
+// asynchronous copy.  A buffer is handed out again once the event recorded
+// after its copy has completed; at most kMaxStage buffers exist, after which
+// the oldest is waited for.  These are host allocations (cudaHostAlloc) made
+// the first few times a larger table is needed; device memory is never
+// allocated.
+struct StageBuf {
+    char* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    int dev = -1;
+    bool busy = false;
+    unsigned long long used = 0;  // order of last use
+};
+constexpr int kMaxStage = 8;
+std::mutex g_stage_mu;
+StageBuf g_stage[kMaxStage];
+unsigned long long g_stage_clock = 0;
+
+wave_status_t stage_acquire(size_t need, int* out)
 {
-    const size_t ntap = h.idx.size();
-    CK(cudaMemcpyAsync(t.cell_start, h.cell_start.data(), h.cell_start.size() * sizeof(int), cudaMemcpyHostToDevice,
-                       s));
-    CK(cudaMemcpyAsync(t.pt_start, h.pt_start.data(), h.pt_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (ntap) {
-        CK(cudaMemcpyAsync(t.idx, h.idx.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(t.ab, h.ab.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(t.slot, h.slot.data(), ntap * sizeof(int), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(t.w, h.w.data(), ntap * sizeof(float), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(t.gw, t.gw_host.data(), ntap * sizeof(float), cudaMemcpyHostToDevice, s));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    int pick = -1, empty = -1, oldest = -1;
+    for (int i = 0; i < kMaxStage; ++i) {
+        StageBuf& b = g_stage[i];
+        if (b.busy) continue;
+        if (!b.p) {
+            if (empty < 0) empty = i;
+            continue;
+        }
+        if (b.dev != dev) continue;
+        if (cudaEventQuery(b.ev) != cudaSuccess) {
+            if (oldest < 0 || b.used < g_stage[oldest].used) oldest = i;
+            continue;
+        }
+        if (b.cap >= need && (pick < 0 || b.cap < g_stage[pick].cap)) pick = i;
+        else if (b.cap < need && empty < 0) empty = -2 - i;  // an idle buffer that is too small: replace it
     }
+    if (pick < 0 && empty != -1) {
+        const int i = empty >= 0 ? empty : -2 - empty;
+        StageBuf& b = g_stage[i];
+        if (b.p) {
+            cudaFreeHost(b.p);
+            cudaEventDestroy(b.ev);
+            b = StageBuf();
+        }
+        const size_t cap = std::max<size_t>(need, 1 << 16);
+        void* p = nullptr;
+        CK(cudaHostAlloc(&p, cap, cudaHostAllocPortable));
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaFreeHost(p);
+            (void)cudaGetLastError();
+            return WAVE_ERR_CUDA;
+        }
+        b.p = static_cast<char*>(p);
+        b.cap = cap;
+        b.ev = ev;
+        b.dev = dev;
+        pick = i;
+    }
+    if (pick < 0) {
+        // every buffer of this device is in flight (or none fits): wait for the oldest one
+        if (oldest < 0) return WAVE_ERR_CUDA;  // all buffers belong to busy calls of other devices
+        StageBuf& b = g_stage[oldest];
+        CK(cudaEventSynchronize(b.ev));
+        if (b.cap < need) {
+            cudaFreeHost(b.p);
+            void* p = nullptr;
+            b.p = nullptr;
+            b.cap = 0;
+            CK(cudaHostAlloc(&p, need, cudaHostAllocPortable));
+            b.p = static_cast<char*>(p);
+            b.cap = need;
+        }
+        pick = oldest;
+    }
+    g_stage[pick].busy = true;
+    g_stage[pick].used = ++g_stage_clock;
+    *out = pick;
+    return WAVE_OK;
+}
+
+void stage_release(int i, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    cudaEventRecord(g_stage[i].ev, s);
+    g_stage[i].busy = false;
+}
+
+// Uploads both tap tables with one copy: the source and receiver arrays are
+// carved back to back, so the staged image mirrors that whole region (the
+// injection factors in it are filled on the device afterwards).
+wave_status_t upload_taps(Layout& L, cudaStream_t s)
+{
+    char* base = reinterpret_cast<char*>(L.ts.cell_start);
+    char* end = reinterpret_cast<char*>(L.tr.pt_start + L.hr.pt_start.size());
+    const size_t n = (size_t)(end - base);
+    int sb = -1;
+    wave_status_t st = stage_acquire(n, &sb);
+    if (st) return st;
+    char* h = g_stage[sb].p;
+    auto put = [&](const void* dst, const void* src, size_t bytes) {
+        if (bytes) memcpy(h + (reinterpret_cast<const char*>(dst) - base), src, bytes);
+    };
+    for (int k = 0; k < 2; ++k) {
+        const HostTaps& ht = k ? L.hr : L.hs;
+        const DevTaps& t = k ? L.tr : L.ts;
+        const size_t ntap = ht.idx.size();
+        put(t.cell_start, ht.cell_start.data(), ht.cell_start.size() * sizeof(int));
+        put(t.pt_start, ht.pt_start.data(), ht.pt_start.size() * sizeof(int));
+        put(t.idx, ht.idx.data(), ntap * sizeof(int));
+        put(t.ab, ht.ab.data(), ntap * sizeof(int));
+        put(t.slot, ht.slot.data(), ntap * sizeof(int));
+        put(t.w, ht.w.data(), ntap * sizeof(float));
+        put(t.gw, t.gw_host.data(), ntap * sizeof(float));
+    }
+    const cudaError_t e = cudaMemcpyAsync(base, h, n, cudaMemcpyHostToDevice, s);
+    stage_release(sb, s);
+    CK(e);
     return WAVE_OK;
 }
 
@@ -306,25 +427,18 @@ float sponge_coefficient(const Dims& d)
     return (float)(3.0 * log(1000.0) * d.h / (4.0 * d.dt * d.vref * nb * nb * nb));
 }
 
-// Uploads tables, prepares the model, validates it, fills the injection
-// factors and encodes the TMA maps.
+// Uploads tables, prepares the model, queues its validation (non-finite
+// velocities and the stability limit set bits of the device error word; the
+// host does not wait for them), fills the injection factors and encodes the
+// TMA maps.
 wave_status_t setup(Layout& L, const float* vel, cudaStream_t s)
 {
-    wave_status_t st = upload_taps(L.hs, L.ts, s);
+    wave_status_t st = upload_taps(L, s);
     if (st) return st;
-    st = upload_taps(L.hr, L.tr, s);
-    if (st) return st;
-    CK(cudaMemsetAsync(L.err, 0, 4 * sizeof(int), s));
-    CK(cudaMemsetAsync(L.vmax, 0, sizeof(float), s));
+    CK(cudaMemsetAsync(L.err, 0, sizeof(WsHeader), s));  // error word, misfit and vmax
     launch_prep(L.d, vel, L.kap, L.vmax, L.err, s);
+    launch_check_cfl(L.vmax, (double)L.d.dt / L.d.h, courant_limit(L.d.ndim), L.err, s);
     CK(cudaGetLastError());
-    int herr = 0;
-    float hvmax = 0.0f;
-    CK(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&hvmax, L.vmax, sizeof(float), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (herr & kErrNonFinite) return WAVE_ERR_NONFINITE;
-    if ((double)L.d.dt * hvmax / L.d.h > courant_limit(L.d.ndim)) return WAVE_ERR_CFL;
     const float ceps = sponge_coefficient(L.d);
     const double h = L.d.h, dt = L.d.dt;
     // Forward source injection adds dt^2 w q / (h^ndim (m + e)) = kap h^(2-ndim) w q / (1 + eps).
@@ -427,24 +541,50 @@ void adj_step(const Layout& L, int cur, int prev, int k, const float* amp_a, con
     launch_step(L.t, L.d.ndim, true, a, &L.maps, s);
 }
 
-wave_status_t finish(const Layout& L, cudaStream_t s)
-{
-    CK(cudaGetLastError());
-    int herr = 0;
-    CK(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (herr & kErrTimeout) return WAVE_ERR_TIMEOUT;
-    if (herr & kErrNonFinite) return WAVE_ERR_NONFINITE;
-    if (herr) return WAVE_ERR_CUDA;
-    return WAVE_OK;
-}
-
 wave_status_t check_work(const Layout& L, void* work, size_t work_bytes)
 {
     if (L.bytes > 0 && (!work || work_bytes < L.bytes)) return WAVE_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(work) % 256) return WAVE_ERR_WORKSPACE;
     return WAVE_OK;
 }
+
+// Status of a device error word; the stability limit takes precedence over
+// non-finite results, which an unstable run produces.
+wave_status_t status_of(int herr)
+{
+    if (herr & kErrTimeout) return WAVE_ERR_TIMEOUT;
+    if (herr & kErrCfl) return WAVE_ERR_CFL;
+    if (herr & kErrNonFinite) return WAVE_ERR_NONFINITE;
+    if (herr) return WAVE_ERR_CUDA;
+    return WAVE_OK;
+}
+
+// Synchronous end of a call (autotuner): waits and reads the error word.
+wave_status_t finish(const Layout& L, cudaStream_t s)
+{
+    CK(cudaGetLastError());
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return status_of(herr);
+}
+
+// A call with no shots queues no work; it still clears the header of a
+// usable workspace, so that wave_status_wait reports success for it.
+wave_status_t clear_header(const Layout& L, void* work, size_t work_bytes, cudaStream_t s)
+{
+    if (work && check_work(L, work, work_bytes) == WAVE_OK) CK(cudaMemsetAsync(L.err, 0, sizeof(WsHeader), s));
+    return WAVE_OK;
+}
+
+// Asynchronous end of a call: launch errors are reported now, device-side
+// errors through wave_status_wait.
+wave_status_t queued()
+{
+    CK(cudaGetLastError());
+    return WAVE_OK;
+}
+
 
 // Runs the binomial checkpoint schedule without copying states: a restore
 // only renames which buffers hold (u^j, u^{j-1}), the last two steps of an
@@ -553,6 +693,18 @@ wave_status_t wave_workspace_size(const wave_grid_t* grid, int op, int nshot, in
     return WAVE_OK;
 }
 
+wave_status_t wave_status_wait(const void* work, void* stream, double* misfit)
+{
+    if (!work) return WAVE_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader h;
+    memset(&h, 0, sizeof(h));
+    CK(cudaMemcpyAsync(&h, work, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (misfit) *misfit = h.misfit;
+    return status_of(h.err[0]);
+}
+
 wave_status_t wave_forward(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
                            const float* wavelet, int nrec, const float* rec_xyz, float* data, void* work,
                            size_t work_bytes, void* stream)
@@ -561,7 +713,7 @@ wave_status_t wave_forward(const wave_grid_t* grid, const float* vel, int nshot,
     Layout L;
     wave_status_t st = plan(grid, 0, nshot, nsrc, src_xyz, nrec, rec_xyz, 0, 0, work, L);
     if (st) return st;
-    if (nshot == 0) return WAVE_OK;
+    if (nshot == 0) return clear_header(L, work, work_bytes, s);
     if (!vel || (nsrc && !wavelet) || (nrec && !data)) return WAVE_ERR_ARG;
     if ((st = check_work(L, work, work_bytes))) return st;
     if ((st = setup(L, vel, s))) return st;
@@ -578,7 +730,7 @@ wave_status_t wave_forward(const wave_grid_t* grid, const float* vel, int nshot,
         launch_finalize(L.tr.l, L.slots_rec, nshot, L.d.nt, data, s);
         launch_nan_scan(data, (long long)nshot * L.d.nt * nrec, L.err, s);
     }
-    return finish(L, s);
+    return queued();
 }
 
 wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot, int nsrc, const float* src_xyz,
@@ -589,7 +741,7 @@ wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot,
     Layout L;
     wave_status_t st = plan(grid, 1, nshot, nsrc, src_xyz, nrec, rec_xyz, 0, 0, work, L);
     if (st) return st;
-    if (nshot == 0) return WAVE_OK;
+    if (nshot == 0) return clear_header(L, work, work_bytes, s);
     if (!vel || (nrec && !resid) || (nsrc && !src_out)) return WAVE_ERR_ARG;
     if ((st = check_work(L, work, work_bytes))) return st;
     if ((st = setup(L, vel, s))) return st;
@@ -606,7 +758,7 @@ wave_status_t wave_adjoint(const wave_grid_t* grid, const float* vel, int nshot,
         launch_finalize(L.ts.l, L.slots_src, nshot, L.d.nt, src_out, s);
         launch_nan_scan(src_out, (long long)nshot * L.d.nt * nsrc, L.err, s);
     }
-    return finish(L, s);
+    return queued();
 }
 
 }  // extern "C"
@@ -630,8 +782,8 @@ wave_status_t gradient_impl(const wave_grid_t* grid, const float* vel, int nshot
     if ((st = check_work(L, work, work_bytes))) return st;
     const Dims& d = L.d;
     if (nshot == 0) {
+        CK(cudaMemsetAsync(L.err, 0, sizeof(WsHeader), s));
         CK(cudaMemsetAsync(grad, 0, d.phys * sizeof(float), s));
-        CK(cudaStreamSynchronize(s));
         if (misfit) *misfit = 0.0;
         return WAVE_OK;
     }
@@ -687,11 +839,10 @@ wave_status_t gradient_impl(const wave_grid_t* grid, const float* vel, int nshot
     launch_nan_scan(grad, d.phys, L.err, s);
     if (!given && d_syn && ndata)
         CK(cudaMemcpyAsync(d_syn, L.dsyn, ndata * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    double hm = 0.0;
-    if (!given) CK(cudaMemcpyAsync(&hm, L.misfit, sizeof(double), cudaMemcpyDeviceToHost, s));
-    st = finish(L, s);
-    if (st == WAVE_OK && misfit) *misfit = given ? 0.0 : hm;
-    return st;
+    // the misfit lands in the caller's host double when the stream gets there
+    // (a copy into pageable memory completes before cudaMemcpyAsync returns)
+    if (misfit) CK(cudaMemcpyAsync(misfit, L.misfit, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return queued();
 }
 
 }  // namespace
@@ -727,7 +878,7 @@ wave_status_t wave_born(const wave_grid_t* grid, const float* vel, int nshot, in
     Layout L;
     wave_status_t st = plan(grid, 3, nshot, nsrc, src_xyz, nrec, rec_xyz, 0, 0, work, L);
     if (st) return st;
-    if (nshot == 0) return WAVE_OK;
+    if (nshot == 0) return clear_header(L, work, work_bytes, s);
     if (!vel || !dm || (nsrc && !wavelet) || (nrec && !data)) return WAVE_ERR_ARG;
     if ((st = check_work(L, work, work_bytes))) return st;
     L.t.vf = 0;  // the direct 2D kernel carries the scattering source
@@ -767,7 +918,7 @@ wave_status_t wave_born(const wave_grid_t* grid, const float* vel, int nshot, in
         launch_finalize(L.tr.l, L.slots_rec, nshot, L.d.nt, data, s);
         launch_nan_scan(data, (long long)nshot * L.d.nt * nrec, L.err, s);
     }
-    return finish(L, s);
+    return queued();
 }
 
 wave_status_t wave_ricker(float f0, float dt, int nt, float* out, void* stream)

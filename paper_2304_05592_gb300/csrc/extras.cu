@@ -1,8 +1,8 @@
 // extras.cu -- data conditioning and model-update kernels around the wave
 // solver: the low-cut wavelet and band-limited noise of the paper's FWI
 // experiment (section "Deep priors and normalizing flows": a Ricker wavelet
-// with no energy below 4 Hz and additive coloured Gaussian noise with the
-// bandwidth of the noise-free data), and the vector updates of an FWI
+// stripped of its content under 4 Hz, plus additive coloured Gaussian noise
+// whose band matches the clean data's), and the vector updates of an FWI
 // iteration (v <- v + a d, then clamping to velocity bounds).
 #include <cuda_runtime.h>
 #include <math.h>

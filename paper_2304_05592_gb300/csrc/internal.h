@@ -23,7 +23,8 @@ constexpr float kC4 = -1.0f / 560.0f;
 // Device error word bits.
 enum : int {
     kErrNonFinite = 1,  // velocity not finite/positive or NaN in a result
-    kErrTimeout = 2     // a bounded wait ran out
+    kErrTimeout = 2,    // a bounded wait ran out
+    kErrCfl = 4         // dt vmax / h above the stability limit
 };
 
 // Padded geometry of one shot's field.  Fields are stored [Nz][Ny][P] floats
@@ -127,6 +128,8 @@ struct StepArgs {
 // Kernel launchers (kernels.cu).
 void launch_step(const Tiling& t, int ndim, bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s);
 void launch_prep(const Dims& d, const float* vel, float* kap, float* vmax, int* err, cudaStream_t s);
+// Sets kErrCfl in *err when dt * (*vmax) / h exceeds limit (one thread).
+void launch_check_cfl(const float* vmax, double dt_over_h, double limit, int* err, cudaStream_t s);
 void launch_tapfac(const Dims& d, const TapList& l, const float* kap, float scale_inj, float ceps,
                    cudaStream_t s);
 void launch_finalize(const TapList& l, const float* slots, int nshot, int nt, float* out, cudaStream_t s);

@@ -14,6 +14,7 @@
 
 #include "internal.h"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace wave {
 
@@ -38,125 +39,6 @@ __device__ __forceinline__ float leap_src(float c, float um, float lap, float ka
     float num = fmaf(kap, lap, fmaf(eps, um, 2.0f * c - um)) - src;
     return num * __frcp_rn(1.0f + eps);
 }
-
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ float f4(const float4& v, int i)
-{
-    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
-
-__device__ __forceinline__ void store_bf16x4(__nv_bfloat16* p, const float* o)
-{
-    __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
-    __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
-    uint2 v;
-    v.x = *reinterpret_cast<uint32_t*>(&lo);
-    v.y = *reinterpret_cast<uint32_t*>(&hi);
-    *reinterpret_cast<uint2*>(p) = v;
-}
-
-__device__ __forceinline__ void unpack_bf16x4(uint2 v, float* o)
-{
-    __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&v.x);
-    __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&v.y);
-    float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-    o[0] = a.x;
-    o[1] = a.y;
-    o[2] = b.x;
-    o[3] = b.y;
-}
-
-// ---------------------------------------------------------------------------
-// mbarrier and TMA (inline PTX, sm_90+ forms that sm_103a keeps).
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Orders this thread's earlier generic-proxy accesses to shared memory before
-// later async-proxy (TMA) writes to it.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-
-// Plain arrival (release at CTA scope), used by consumers to free a ring slot.
-__device__ __forceinline__ void mbar_arrive(uint64_t* b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on a barrier phase: false after ~4M polls (seconds), so a copy
-// that never lands turns into an error status instead of a hung GPU.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
-{
-    for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try(b, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0, int c1)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
-        "r"(c3)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3, int c4)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
-        "r"(c3), "r"(c4)
-        : "memory");
-}
-
-// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Sparse part of a step, run by the CTA that owns a tile after its points are
@@ -1793,15 +1675,30 @@ static int num_sms()
     return n;
 }
 
+// True on the first call for the current device with this flag array (one
+// flag per device): kernel attributes such as the dynamic shared-memory limit
+// are per device, so each device gets its own first call.
+constexpr int kMaxDev = 64;
+static bool first_on_device(bool* done)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    if (done[dev]) return false;
+    done[dev] = true;
+    return true;
+}
+
 template <int TZ, int R, int NST, bool ADJ>
 static void launch_2d(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
     constexpr int STAGE = (TZ + 8) * (kTX + 8) + (ADJ ? 4 : 2) * TZ * kTX;
     constexpr size_t smem = (size_t)NST * STAGE * 4 + 128;
-    static bool configured = false;
-    if (!configured) {
+    static bool configured[kMaxDev] = {};
+    if (first_on_device(configured)) {
         cudaFuncSetAttribute(k_step2d_tma<TZ, R, NST, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
     }
     const int ntz = (a.Nz + TZ - 1) / TZ;
     const long long ntile = (long long)a.nshot * ntz * a.ncx;
@@ -1872,11 +1769,10 @@ template <int TY, int TZC, int NR>
 static void launch_3d_ws(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
     constexpr size_t smem = (size_t)NR * (TY + 8) * (kTX + 8) * 4 + 128;
-    static bool configured = false;
-    if (!configured) {
+    static bool configured[kMaxDev] = {};
+    if (first_on_device(configured)) {
         cudaFuncSetAttribute(k_step3d_ws<TY, TZC, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_step3d_ws<TY, TZC, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
     }
     const int ntz = (a.Nz + TZC - 1) / TZC;
     dim3 grid(a.ncx, (a.Ny + TY - 1) / TY, ntz * a.nshot);
@@ -1888,12 +1784,11 @@ template <int TY, int TZC, int NR>
 static void launch_3d_tma(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
     constexpr size_t smem = (size_t)NR * (TY + 8) * (kTX + 8) * 4 + 128;
-    static bool configured = false;
-    if (!configured) {
+    static bool configured[kMaxDev] = {};
+    if (first_on_device(configured)) {
         cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
     }
     const int ntz = (a.Nz + TZC - 1) / TZC;
     dim3 grid(a.ncx, (a.Ny + TY - 1) / TY, ntz * a.nshot);
@@ -1905,10 +1800,9 @@ template <int TZ, int BZ, int G, bool ADJ>
 static void launch_2d_group(const StepArgs& a, cudaStream_t s)
 {
     constexpr size_t smem = (size_t)(2 * (TZ + 8) * (kTX + 8) + (ADJ ? TZ * kTX : 0)) * 4;
-    static bool configured = false;
-    if (!configured) {
+    static bool configured[kMaxDev] = {};
+    if (first_on_device(configured)) {
         cudaFuncSetAttribute(k_step2d_sg<TZ, BZ, G, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
     }
     dim3 grid(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
     k_step2d_sg<TZ, BZ, G, ADJ><<<grid, dim3(32, BZ), smem, s>>>(a);
@@ -1919,10 +1813,9 @@ static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStr
 {
     constexpr size_t smem = (size_t)(2 * ((TZ + 8) * (kTX + 8) + ((FL & 1) ? TZ * kTX : 0)) + (ADJ ? TZ * kTX : 0) +
                                      ((FL & 2) ? 2 * TZ * kTX : 0)) * 4 + 128;
-    static bool configured = false;
-    if (!configured) {
+    static bool configured[kMaxDev] = {};
+    if (first_on_device(configured)) {
         cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, FL, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
     }
     // launched with programmatic stream serialization: consecutive steps overlap the
     // launch and set-up of one with the last CTAs of the other (see the kernel)
@@ -1936,7 +1829,8 @@ static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStr
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_step2d_sgt<TZ, BZ, G, FL, ADJ>, *maps, a);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_step2d_sgt<TZ, BZ, G, FL, ADJ>, *maps, a);
+    if (e != cudaSuccess) note_cuda_error(e);  // the caller's cudaGetLastError check reports it
 }
 
 template <int TZ, int BZ, bool ADJ>
@@ -2151,6 +2045,19 @@ void launch_prep(const Dims& d, const float* vel, float* kap, float* vmax, int* 
     if (blocks > 152 * 16) blocks = 152 * 16;
     count_launch();
     k_prep<<<(int)blocks, 256, 0, s>>>(d, vel, kap, vmax, err);
+}
+
+// The stability check on the device, so that a call need not wait for the
+// model's maximum velocity on the host: compares in double, as the host did.
+__global__ void k_check_cfl(const float* vmax, double dt_over_h, double limit, int* err)
+{
+    if (threadIdx.x == 0 && dt_over_h * (double)*vmax > limit) atomicOr(err, kErrCfl);
+}
+
+void launch_check_cfl(const float* vmax, double dt_over_h, double limit, int* err, cudaStream_t s)
+{
+    count_launch();
+    k_check_cfl<<<1, 32, 0, s>>>(vmax, dt_over_h, limit, err);
 }
 
 // fac = w * scale * kap / (1 + eps) at each tap's grid point: the amount that

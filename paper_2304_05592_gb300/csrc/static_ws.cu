@@ -11,10 +11,8 @@
 // The array is a file-scope __device__ array of WAVE_STATIC_WORKSPACE_BYTES:
 // every GPU on which the library's module is loaded holds it until the
 // process exits.  In host code its name is only a host-side stand-in for the
-// symbol, so the device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and passed on as the
-// workspace pointer.
-#include <mutex>
+// symbol, so each call looks up the device address on the current device with
+// cudaGetSymbolAddress and passes it on as the workspace pointer.
 
 #include "internal.h"
 
@@ -22,28 +20,18 @@ namespace {
 
 __device__ __align__(256) unsigned char g_scratch[WAVE_STATIC_WORKSPACE_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (looked up on first use).
+// Device address of g_scratch on the current device.  Looked up on every call
+// (cudaGetSymbolAddress allocates nothing and is cheap once the module is
+// loaded on the device) rather than cached, so the address stays right after a
+// cudaDeviceReset or any other teardown of the device's context.
 wave_status_t scratch_address(void** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        (void)cudaGetLastError();
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+        wave::note_cuda_error(cudaGetLastError());
         return WAVE_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return WAVE_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return WAVE_OK;
 }
 
@@ -62,6 +50,10 @@ extern "C" wave_status_t wave_forward_static(const wave_grid_t* grid, const floa
     // wave_forward clears every part of the workspace that must start at zero
     // (both wavefields and the first row of receiver slots) before its time
     // loop, so what an earlier call left in the array does not leak into this one.
-    return wave_forward(grid, vel, nshot, nsrc, src_xyz, wavelet, nrec, rec_xyz, data, scratch,
-                        WAVE_STATIC_WORKSPACE_BYTES, stream);
+    st = wave_forward(grid, vel, nshot, nsrc, src_xyz, wavelet, nrec, rec_xyz, data, scratch,
+                      WAVE_STATIC_WORKSPACE_BYTES, stream);
+    if (st || nshot == 0) return st;
+    // this entry point returns with its results complete: wait for the
+    // stream and report the device-side errors of the call
+    return wave_status_wait(scratch, stream, nullptr);
 }

@@ -1,8 +1,8 @@
 """FWI outer loops on the batched solver.
 
 * ``fwi_subsampled``: gradient descent where each iteration uses a few shots
-  drawn at random with replacement, as the paper does "to limit the number of
-  wave-equation solves" (arxiv 2304.05592, section "Putting it all together":
+  drawn at random with replacement, which is how the paper keeps the count of
+  wave-equation solves down (arxiv 2304.05592, section "Putting it all together":
   four random shots per iteration, 200 iterations, about 25 passes through the
   data); the step along the subset gradient is found by backtracking on the
   subset misfit, and models stay within velocity bounds.

@@ -103,6 +103,15 @@ def _lib():
         lib.wave_workspace_size_batch.restype = I
         lib.wave_gradient_batch.argtypes = [ctypes.POINTER(wave_problem_t), I, I, I, I, P, ctypes.c_size_t, P]
         lib.wave_gradient_batch.restype = I
+        lib.wave_autotune_batch.argtypes = [ctypes.POINTER(wave_problem_t), I, I, I, P, ctypes.c_size_t, P,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        lib.wave_autotune_batch.restype = I
+        lib.wave_set_batch_variant.argtypes = [I, I]
+        lib.wave_set_batch_variant.restype = I
+        lib.wave_batch_variant_count.argtypes = []
+        lib.wave_batch_variant_count.restype = I
+        lib.wave_status_wait.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
+        lib.wave_status_wait.restype = I
         L = ctypes.c_longlong
         F = ctypes.c_float
         lib.wave_lowcut_work_bytes.argtypes = [I]
@@ -191,6 +200,27 @@ def _ptr(a: np.ndarray) -> ctypes.c_void_p:
     return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
 
 
+def wave_status_wait(work: torch.Tensor, stream=None):
+    """Waits for the stream and returns (status, misfit) of the last call
+    queued on the workspace `work` (0 = success; the misfit of wave_gradient)."""
+    phi = ctypes.c_double(0.0)
+    st = _lib().wave_status_wait(ctypes.c_void_p(work.data_ptr()), _stream(stream), ctypes.byref(phi))
+    return int(st), float(phi.value)
+
+
+def _finish(st: int, work: torch.Tensor, stream, name: str, sync: bool) -> float:
+    """Raises on a host-side error; with sync, waits for the call and raises on a
+    device-side error; returns the misfit the workspace holds (0 without sync)."""
+    if st:
+        raise WaveError(st, name)
+    if not sync:
+        return 0.0
+    st, phi = wave_status_wait(work, stream)
+    if st:
+        raise WaveError(st, name)
+    return phi
+
+
 def wave_workspace_size(grid: Grid, op: int, src_xyz, rec_xyz, store: int = STORE_CHECKPOINT,
                         nsnap: int = 1) -> int:
     src = _host_xyz(src_xyz, grid.ndim)
@@ -209,8 +239,10 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
 
 
 def wave_forward(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, data=None,
-                 stream=None) -> torch.Tensor:
-    """Shot records [nshot][nt][nrec] = F(m) q for every shot."""
+                 stream=None, work: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
+    """Shot records [nshot][nt][nrec] = F(m) q for every shot.  With
+    sync=False the call is only queued on the stream (pass `work` and check it
+    later with wave_status_wait)."""
     src = _host_xyz(src_xyz, grid.ndim)
     rec = _host_xyz(rec_xyz, grid.ndim)
     ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
@@ -222,12 +254,12 @@ def wave_forward(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, 
         data = torch.empty((ns, grid.nt, nrec), dtype=torch.float32, device=vel.device)
     pd = _dev(data, "data", (ns, grid.nt, nrec))
     nbytes = wave_workspace_size(grid, OP_FORWARD, src, rec)
-    work = _workspace(nbytes, vel.device)
+    if work is None or work.numel() < nbytes:
+        work = _workspace(nbytes, vel.device)
     g = grid.c()
     st = _lib().wave_forward(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pd,
                              work.data_ptr(), work.numel(), _stream(stream))
-    if st:
-        raise WaveError(st, "wave_forward")
+    _finish(st, work, stream, "wave_forward", sync and ns > 0)
     return data
 
 
@@ -257,7 +289,7 @@ def wave_forward_static(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.T
 
 
 def wave_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, rec_xyz, resid: torch.Tensor, src_out=None,
-                 stream=None) -> torch.Tensor:
+                 stream=None, work: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
     """F(m)' r for every shot: [nshot][nt][nsrc]."""
     src = _host_xyz(src_xyz, grid.ndim)
     rec = _host_xyz(rec_xyz, grid.ndim)
@@ -268,19 +300,21 @@ def wave_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, rec_xyz, resid: torch.T
         src_out = torch.empty((ns, grid.nt, nsrc), dtype=torch.float32, device=vel.device)
     po = _dev(src_out, "src_out", (ns, grid.nt, nsrc))
     nbytes = wave_workspace_size(grid, OP_ADJOINT, src, rec)
-    work = _workspace(nbytes, vel.device)
+    if work is None or work.numel() < nbytes:
+        work = _workspace(nbytes, vel.device)
     g = grid.c()
     st = _lib().wave_adjoint(ctypes.byref(g), pv, ns, nsrc, _ptr(src), nrec, _ptr(rec), pr, po, work.data_ptr(),
                              work.numel(), _stream(stream))
-    if st:
-        raise WaveError(st, "wave_adjoint")
+    _finish(st, work, stream, "wave_adjoint", sync and ns > 0)
     return src_out
 
 
 def wave_gradient(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz, d_obs: torch.Tensor,
                   store: int = STORE_CHECKPOINT, nsnap: int = 64, grad=None, want_dsyn: bool = False,
-                  work: torch.Tensor | None = None, stream=None, wrt: int = WRT_SLOWNESS2):
-    """Returns (misfit, dPhi/dm (or dPhi/dv with wrt=WRT_VELOCITY) [phys shape], d_syn or None)."""
+                  work: torch.Tensor | None = None, stream=None, wrt: int = WRT_SLOWNESS2, sync: bool = True):
+    """Returns (misfit, dPhi/dm (or dPhi/dv with wrt=WRT_VELOCITY) [phys shape], d_syn or None).
+    With sync=False the call is only queued (misfit None; pass `work` and read
+    the status and misfit later with wave_status_wait)."""
     src = _host_xyz(src_xyz, grid.ndim)
     rec = _host_xyz(rec_xyz, grid.ndim)
     ns, nsrc, nrec = src.shape[0], src.shape[1], rec.shape[1]
@@ -295,13 +329,11 @@ def wave_gradient(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor,
     nbytes = wave_workspace_size(grid, OP_GRADIENT, src, rec, store, nsnap)
     if work is None or work.numel() < nbytes:
         work = _workspace(nbytes, vel.device)
-    phi = ctypes.c_double(0.0)
     g = grid.c()
     st = _lib().wave_gradient(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), po, pg, pds,
-                              ctypes.byref(phi), store, nsnap, wrt, work.data_ptr(), work.numel(), _stream(stream))
-    if st:
-        raise WaveError(st, "wave_gradient")
-    return phi.value, grad, dsyn
+                              None, store, nsnap, wrt, work.data_ptr(), work.numel(), _stream(stream))
+    phi = _finish(st, work, stream, "wave_gradient", sync)
+    return (phi if sync else None), grad, dsyn
 
 
 def wave_jacobian_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec_xyz,
@@ -321,8 +353,7 @@ def wave_jacobian_adjoint(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch
     g = grid.c()
     st = _lib().wave_jacobian_adjoint(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pr, pg, store,
                                       nsnap, wrt, work.data_ptr(), work.numel(), _stream(stream))
-    if st:
-        raise WaveError(st, "wave_jacobian_adjoint")
+    _finish(st, work, stream, "wave_jacobian_adjoint", True)
     return grad
 
 
@@ -342,8 +373,7 @@ def wave_born(grid: Grid, vel: torch.Tensor, src_xyz, wavelet: torch.Tensor, rec
     g = grid.c()
     st = _lib().wave_born(ctypes.byref(g), pv, ns, nsrc, _ptr(src), pw, nrec, _ptr(rec), pdm, pd, work.data_ptr(),
                           work.numel(), _stream(stream))
-    if st:
-        raise WaveError(st, "wave_born")
+    _finish(st, work, stream, "wave_born", ns > 0)
     return data
 
 
@@ -476,6 +506,38 @@ def wave_gradient_batch(problems, store: int = STORE_BF16, wrt: int = WRT_SLOWNE
     if st:
         raise WaveError(st, "wave_gradient_batch")
     return [arr[i].misfit for i in range(len(problems))], grads
+
+
+def wave_autotune_batch(problems, store: int = STORE_BF16, steps: int = 200, work: torch.Tensor | None = None,
+                        stream=None):
+    """Times every sweep-kernel variant on the first `steps` steps of this
+    batch and records the fastest pair for batches of its shapes.  Returns
+    (forward variant, adjoint variant)."""
+    grads = [None] * len(problems)
+    arr = _problem_array(problems, grads)
+    nbytes = ctypes.c_size_t(0)
+    st = _lib().wave_workspace_size_batch(arr, len(problems), store, ctypes.byref(nbytes))
+    if st:
+        raise WaveError(st, "wave_workspace_size_batch")
+    if work is None or work.numel() < nbytes.value:
+        work = _workspace(nbytes.value, problems[0].vel.device)
+    bf, ba = ctypes.c_int(-1), ctypes.c_int(-1)
+    st = _lib().wave_autotune_batch(arr, len(problems), store, steps, work.data_ptr(), work.numel(), _stream(stream),
+                                    ctypes.byref(bf), ctypes.byref(ba))
+    if st:
+        raise WaveError(st, "wave_autotune_batch")
+    return bf.value, ba.value
+
+
+def wave_batch_variant_count() -> int:
+    return int(_lib().wave_batch_variant_count())
+
+
+def wave_set_batch_variant(fwd: int, adj: int) -> None:
+    """Forces the uneven batch's sweep kernels (both -1: back to the tuned choice)."""
+    st = _lib().wave_set_batch_variant(fwd, adj)
+    if st:
+        raise WaveError(st, "wave_set_batch_variant")
 
 
 def wave_workspace_size_batch(problems, store: int = STORE_BF16) -> int:

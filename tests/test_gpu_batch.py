@@ -84,3 +84,64 @@ def test_batch_autograd(batch):
     _, gv = wave.wave_gradient_batch(probs, wrt=wave.WRT_VELOCITY, use_graph=False)
     for bp, g in zip(probs, gv):
         assert float((bp.vel.grad - g).norm() / g.norm()) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def wide_batch():
+    # grids of 1-2 tiles across and 3-9 tile rows of 16 (ragged both ways), nt 687-1160
+    probs = synth.uneven_batch(seed=12, nshot=4, scale=0.3)
+    out = []
+    for p in probs:
+        q = oracle.ricker(p.f0, p.dt, p.nt).astype(np.float32)
+        dobs = oracle.forward(ogrid(p), p.vel, p.src, q[None, :, None], p.rec)[0].astype(np.float32)
+        v0 = (p.vel * 1.03).astype(np.float32)
+        phi_r, g_r = oracle.gradient(ogrid(p), v0, p.src, q[None, :, None], p.rec, dobs)
+        out.append((p, q, dobs, v0, phi_r, g_r))
+    return out
+
+
+@pytest.fixture
+def restore_batch_variant():
+    yield
+    wave.wave_set_batch_variant(-1, -1)
+
+
+def test_every_sweep_variant_matches_oracle(wide_batch, restore_batch_variant):
+    """Each sweep kernel (direct loads; TMA producer/consumer with 16- or
+    32-row tiles, 2-8 consumer warps, 2-3 stages) gives the oracle's misfits
+    and gradients, and all of them agree to rounding of the imaging sums."""
+    assert any(p.nx + 2 * p.nb > 128 for p, *_ in wide_batch)  # two tile columns or more
+    probs = _problems([b[:4] for b in wide_batch])
+    base = None
+    for v in range(wave.wave_batch_variant_count()):
+        wave.wave_set_batch_variant(v, v)
+        misfits, grads = wave.wave_gradient_batch(probs, store=wave.STORE_FP32, use_graph=False)
+        for (p, q, dobs, v0, phi_r, g_r), phi, gr in zip(wide_batch, misfits, grads):
+            assert abs(phi - phi_r) <= 3e-4 * phi_r, (v, phi, phi_r)
+            assert rel(gr.cpu().numpy(), g_r) < 1e-3, (v, rel(gr.cpu().numpy(), g_r))
+        if base is None:
+            base = grads
+        else:
+            for a, b in zip(grads, base):
+                assert float((a - b).norm() / b.norm()) < 1e-5, v
+
+
+def test_autotuned_batch_matches_oracle_bf16(wide_batch, restore_batch_variant):
+    probs = _problems([b[:4] for b in wide_batch])
+    vf, va = wave.wave_autotune_batch(probs, store=wave.STORE_BF16, steps=50)
+    n = wave.wave_batch_variant_count()
+    assert 0 <= vf < n and 0 <= va < n
+    misfits, grads = wave.wave_gradient_batch(probs, store=wave.STORE_BF16)
+    errs = []
+    for (p, q, dobs, v0, phi_r, g_r), phi, gr in zip(wide_batch, misfits, grads):
+        assert abs(phi - phi_r) <= 3e-4 * phi_r
+        errs.append(rel(gr.cpu().numpy(), g_r))
+    print(f"uneven batch, BF16 store, sweeps {vf}/{va}: gradient rel L2 vs oracle {errs}")
+    assert max(errs) < 1e-2
+
+
+def test_forced_variant_pair_must_share_tile_height(restore_batch_variant):
+    with pytest.raises(wave.WaveError):
+        wave.wave_set_batch_variant(0, 1)  # 32-row against 16-row tiles
+    with pytest.raises(wave.WaveError):
+        wave.wave_set_batch_variant(wave.wave_batch_variant_count(), 0)
