@@ -126,6 +126,43 @@ __global__ void k_axpy(long long n, float alpha, const float* __restrict__ x, fl
         y[i] = fmaf(alpha, x[i], y[i]);
 }
 
+__global__ void k_axpby(long long n, float alpha, const float* __restrict__ x, float beta, float* __restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fmaf(alpha, x[i], beta * y[i]);
+}
+
+// Dot product in double: kDotBlocks partial sums over a fixed grid-stride
+// split, then one block adds them in block order (same bits on every run).
+constexpr int kDotBlocks = 256;
+
+__global__ void k_dot_partial(long long n, const float* __restrict__ x, const float* __restrict__ y, double* part)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * kDotBlocks)
+        acc = fma((double)x[i], (double)y[i], acc);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(const double* part, double* out)
+{
+    __shared__ double sh[kDotBlocks];
+    sh[threadIdx.x] = part[threadIdx.x];
+    __syncthreads();
+    for (int w = kDotBlocks / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
 __global__ void k_clamp(long long n, float lo, float hi, float* __restrict__ y)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -192,6 +229,26 @@ wave_status_t wave_axpy(long long n, float alpha, const float* x, float* y, void
     if (n < 0 || !x || !y) return WAVE_ERR_ARG;
     if (n == 0) return WAVE_OK;
     k_axpy<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, alpha, x, y);
+    return launched();
+}
+
+wave_status_t wave_axpby(long long n, float alpha, const float* x, float beta, float* y, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return WAVE_ERR_ARG;
+    if (n == 0) return WAVE_OK;
+    count_launch();
+    k_axpby<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, alpha, x, beta, y);
+    return launched();
+}
+
+wave_status_t wave_dot(long long n, const float* x, const float* y, double* out, void* stream)
+{
+    static_assert(kDotBlocks == WAVE_DOT_PARTIALS, "the header's scratch count");
+    if (n < 0 || !out || (n > 0 && (!x || !y))) return WAVE_ERR_ARG;  // n = 0: out[0] = 0
+    cudaStream_t s = (cudaStream_t)stream;
+    count_launch(2);
+    k_dot_partial<<<kDotBlocks, 256, 0, s>>>(n, x, y, out + 1);
+    k_dot_final<<<1, kDotBlocks, 0, s>>>(out + 1, out);
     return launched();
 }
 
