@@ -247,6 +247,18 @@ wave_status_t wave_add_noise(const float* data, const float* white, int nshot, i
 wave_status_t wave_axpy(long long n, float alpha, const float* x, float* y, void* stream);
 wave_status_t wave_clamp(long long n, float lo, float hi, float* y, void* stream);
 
+/* Vector steps of the least-squares RTM iteration (conjugate gradients on
+ * the normal equations J'J dm = J' dd of judiJacobian, section
+ * "Wave-equation-based inversion"): y = alpha x + beta y, and the dot product
+ * sum_i x_i y_i accumulated in double in a fixed order (the same bits on every
+ * run) into out[0]; out is a device array of 1 + WAVE_DOT_PARTIALS doubles
+ * (the rest is scratch).  n device floats; stream-ordered, no
+ * synchronisation; WAVE_ERR_ARG for n < 0 or a null pointer (x and y may be
+ * null when n = 0, which gives out[0] = 0). */
+#define WAVE_DOT_PARTIALS 256
+wave_status_t wave_axpby(long long n, float alpha, const float* x, float beta, float* y, void* stream);
+wave_status_t wave_dot(long long n, const float* x, const float* y, double* out, void* stream);
+
 /* The bounded wait that the persistent batch sweep uses between tiles, run by
  * one thread on a caller-given device flag: it polls *flag >= want through L2
  * and gives up after a fixed number of polls (a few seconds) or as soon as
@@ -324,9 +336,13 @@ wave_status_t wave_checkpoint_schedule(int nt, int nsnap, long long* fwd_steps, 
  * wave_launch_count: number of kernels this library has launched so far in
  * the process.  wave_profile_start(every): from now on, bracket every
  * `every`-th stencil time-step launch with two CUDA events on its stream
- * (at most 8192 samples).  wave_profile_stop: stops sampling, waits for the
- * sampled events and returns the summed milliseconds and the number of
- * sampled forward and adjoint step launches (any pointer may be NULL). */
+ * (at most 8192 samples); every = 0 instead brackets each run of consecutive
+ * step launches of one kind (forward or adjoint) on one stream, which keeps
+ * the overlap between consecutive launches inside a run (at most 16384 runs;
+ * a run ends at a change of kind or stream or at another library kernel).
+ * wave_profile_stop: stops sampling, waits for the sampled events and returns
+ * the summed milliseconds and the number of forward and adjoint step
+ * launches they cover (any pointer may be NULL). */
 long long wave_launch_count(void);
 wave_status_t wave_profile_start(int every);
 wave_status_t wave_profile_stop(double* fwd_ms, long long* fwd_n, double* adj_ms, long long* adj_n);

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwave.so")
-SOURCES = ["api.cu", "plan.cu", "kernels.cu", "profile.cu", "static_ws.cu", "batch.cu", "fno.cu", "extras.cu"]
+SOURCES = ["api.cu", "plan.cu", "kernels.cu", "step2d_zw.cu", "profile.cu", "static_ws.cu", "batch.cu", "fno.cu",
+           "extras.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -152,12 +152,17 @@ constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile h
 // distance NST rows, shot groups fed by TMA (kind 4, fields as kind 2; NST bit
 // 0: the previous level's tile comes by TMA too, bit 1: the sponge factors sit
 // in shared memory instead of registers), or
-// the persistent kernel over (tile, shot) items (kind 5, R = thread rows).
+// the persistent kernel over (tile, shot) items (kind 5, R = thread rows), or
+// the z-window kernel (kind 7, below).
 // With kinds 2 and 4 in the adjoint, the gradient buffer holds one
 // accumulator per shot group; with kind 5, one per CTA segment of a tile.
 struct Variant2D {
     int kind, TZ, R, NST, G;
 };
+// Kind 7: shot groups fed by TMA with the z window of each thread's
+// consecutive rows in registers (G shots per CTA; NST = configuration index
+// of launch_step2d_zw, step2d_zw.cu).
+void launch_step2d_zw(int config, bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s);
 // Number of per-shot/per-group gradient accumulators the adjoint step fills.
 int gradient_accumulators(const struct Tiling& t, int ndim, int nshot);
 int persistent_slots(int v, int ncx, int ntz, int nshot);  // adjoint variant v of kind 5
@@ -174,6 +179,7 @@ void note_cuda_error(cudaError_t e);
 // (profile.cu).  Every launcher above calls count_launch(); launch_step wraps
 // sampled launches in a pair of CUDA events on the launching stream.
 void count_launch(int n = 1);
+void count_step_launch();  // a stencil time step (launch_step)
 bool profile_sample(bool adjoint, cudaStream_t s, cudaEvent_t* stop);
 void profile_close(cudaEvent_t stop, cudaStream_t s);
 

@@ -15,14 +15,10 @@
 #include "internal.h"
 #include "stencil.cuh"
 #include "tma.cuh"
+#include "step_common.cuh"
 
 namespace wave {
 
-__device__ __forceinline__ int sponge_depth(int i, int nb, int n)
-{
-    int d = max(nb - i, i - (nb + n - 1));
-    return max(d, 0);
-}
 
 // One leapfrog update in Courant units:
 //   (1+eps) u+ = 2u - (1-eps) u- + kap * lap,  kap = (v dt/h)^2, eps = eta dt v^2 / 2.
@@ -38,58 +34,6 @@ __device__ __forceinline__ float leap_src(float c, float um, float lap, float ka
 {
     float num = fmaf(kap, lap, fmaf(eps, um, 2.0f * c - um)) - src;
     return num * __frcp_rn(1.0f + eps);
-}
-
-// ---------------------------------------------------------------------------
-// Sparse part of a step, run by the CTA that owns a tile after its points are
-// written: injection into unew, then gathers of unew into slots.  [ib, ie)
-// and [gb, ge) are the tile's ranges in the injection and gather tap lists;
-// sgt, if given, is the tile's gradient accumulator in shared memory, with
-// its first point at (z0, x0).  WARP: the caller is one warp that owns the
-// tile (warp barrier instead of a block barrier).
-template <bool ADJ, bool WARP = false>
-__device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, int gb, int ge, long long so, int tid,
-                                             int nthr, float* sgt = nullptr, int z0 = 0, int x0 = 0)
-{
-    float* un = a.unew + so;
-    if (a.inj.cell_start) {
-        // Taps are sorted by grid point inside each cell: the thread holding the
-        // first tap of a point sums that point's taps in a fixed order and owns
-        // the update, so no atomics are needed and results are repeatable.
-        for (int j = ib + tid; j < ie; j += nthr) {
-            const int i = a.inj.idx[j];
-            if (j > ib && a.inj.idx[j - 1] == i) continue;
-            float add = 0.0f;
-            for (int jj = j; jj < ie && a.inj.idx[jj] == i; ++jj) {
-                const long long ai = (long long)a.inj.ab[jj] + (long long)a.amp_row * a.inj.npts;
-                float amp = a.amp_a[ai];
-                if (a.amp_b) amp -= a.amp_b[ai];
-                add = fmaf(a.inj.fac[jj], amp, add);
-            }
-            const float v = un[i] + add;
-            un[i] = v;
-            if (!ADJ) {
-                // the stored copy of the new level must include the injection
-                if (a.st16) a.st16[so + i] = __float2bfloat16_rn(v);
-                if (a.st32) a.st32[so + i] = v;
-            } else if (a.gacc) {
-                const float uf = a.uf16 ? __bfloat162float(a.uf16[so + i]) : a.uf32[so + i];
-                if (sgt) {
-                    // the tile's gradient accumulator lives in shared memory (2D, shot-group kernel)
-                    const int z = i / a.P, x = i - z * a.P;
-                    sgt[(z - z0) * kTX + (x - x0)] -= uf * add;
-                } else {
-                    a.gacc[so + i] -= uf * add;
-                }
-            }
-        }
-    }
-    if (a.gat.cell_start) {
-        if (WARP) __syncwarp();
-        else __syncthreads();
-        float* row = a.slots + (long long)a.slot_row * a.gat.ntap;
-        for (int j = gb + tid; j < ge; j += nthr) row[a.gat.slot[j]] = a.gat.gw[j] * un[a.gat.idx[j]];
-    }
 }
 
 // Born secondary source of four points: dmv .* (u^{n+1} - 2 u^n + u^{n-1}),
@@ -461,16 +405,12 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
     }
     __syncthreads();
     // Programmatic dependent launch: the next step's CTAs may be scheduled once
-    // every CTA of this grid has started, and this grid touches global memory
+    // every CTA of this grid has started.  Until griddepcontrol.wait (below)
+    // this grid reads only the model, which no step writes and whose writer
+    // finished before the first step of the call started; the fields are read
     // only after the previous kernel in the stream has finished and its writes
     // are visible (both are no-ops for a launch without the attribute).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0) {
-        mbar_expect_tx(&bar[0], kBytes);
-        tma_load_4d(st, mh, &bar[0], x0 - 4, z0 - 4, s0, a.u_buf);
-        if (PT) tma_load_4d(st + SU, mt, &bar[0], x0, z0, s0, a.prev_buf);
-    }
 
     int off[RB];
     bool live[RB], pad[RB];
@@ -503,6 +443,12 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
                 inv[SE ? 0 : rr][e] = iv[e];
             }
         }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], kBytes);
+        tma_load_4d(st, mh, &bar[0], x0 - 4, z0 - 4, s0, a.u_buf);
+        if (PT) tma_load_4d(st + SU, mt, &bar[0], x0, z0, s0, a.prev_buf);
     }
     float* gq = imaging ? a.gacc + (size_t)grp * a.cell : nullptr;
     if (imaging) {
@@ -1716,7 +1662,8 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2}, {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4},
                                    {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0}, {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2},
                                    {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}, {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2},
-                                   {4, 16, 8, 2, 4}};
+                                   {4, 16, 8, 2, 4},  {7, 16, 4, 0, 2}, {7, 16, 4, 1, 4}, {7, 16, 2, 2, 2},
+                                   {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2}, {7, 16, 8, 5, 2}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
@@ -1724,7 +1671,9 @@ static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2
                                    {4, 16, 8, 0, 2}, {4, 16, 8, 0, 4}, {4, 16, 8, 0, 8}, {4, 32, 8, 0, 2},
                                    {4, 32, 8, 0, 4}, {4, 8, 8, 0, 4}, {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0},
                                    {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2}, {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4},
-                                   {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2}, {4, 16, 8, 2, 4}};
+                                   {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2}, {4, 16, 8, 2, 4},  {7, 16, 4, 0, 2},
+                                   {7, 16, 4, 1, 4}, {7, 16, 2, 2, 2}, {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2},
+                                   {7, 16, 8, 5, 2}};
 // 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y, NST = ring
 // slots, G = 1 for the ring without block barriers): kind 0 is the z-march
 // with a shared-memory halo plane, kind 6 the TMA plane ring.
@@ -1903,6 +1852,11 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
                             cudaStream_t s)
 {
     if (ndim == 2) {
+        const Variant2D vi = variant_info(adjoint ? 1 : 0, adjoint ? t.va : t.vf);
+        if (vi.kind == 7) {  // z window in registers (step2d_zw.cu); NST holds its configuration index
+            launch_step2d_zw(vi.NST, adjoint, a, maps, s);
+            return;
+        }
         if (!adjoint) {
             switch (t.vf) {
             case 1: launch_2d<48, 6, 2, false>(a, maps, s); break;
@@ -1999,7 +1953,7 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
 
 void launch_step(const Tiling& t, int ndim, bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
-    count_launch();
+    count_step_launch();
     cudaEvent_t stop;
     const bool timed = profile_sample(adjoint, s, &stop);
     launch_step_raw(t, ndim, adjoint, a, maps, s);

@@ -80,7 +80,7 @@ int gradient_accumulators(const Tiling& t, int ndim, int nshot)
         const int ntz = (t.ncz * t.TZc + v.TZ - 1) / v.TZ;
         return persistent_slots(t.va, t.ncx, ntz, nshot);
     }
-    return v.kind == 2 || v.kind == 4 ? (nshot + v.G - 1) / v.G : nshot;
+    return v.kind == 2 || v.kind == 4 || v.kind == 7 ? (nshot + v.G - 1) / v.G : nshot;
 }
 
 // Interpolation taps of one point: bilinear (2D) / trilinear (3D) weights on

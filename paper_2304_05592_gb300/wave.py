@@ -126,6 +126,10 @@ def _lib():
         lib.wave_axpy.restype = I
         lib.wave_clamp.argtypes = [L, F, F, P, P]
         lib.wave_clamp.restype = I
+        lib.wave_axpby.argtypes = [L, F, P, F, P, P]
+        lib.wave_axpby.restype = I
+        lib.wave_dot.argtypes = [L, P, P, P, P]
+        lib.wave_dot.restype = I
         lib.wave_wait_probe.argtypes = [P, I, P, P, P]
         lib.wave_wait_probe.restype = I
         lib.wave_set_variant.argtypes = [I, I]
@@ -412,7 +416,8 @@ def wave_launch_count() -> int:
 
 
 def wave_profile_start(every: int = 1) -> None:
-    """Bracket every `every`-th stencil step launch with CUDA events."""
+    """Bracket every `every`-th stencil step launch with CUDA events (every = 0:
+    each run of consecutive step launches of one kind, overlap kept)."""
     st = _lib().wave_profile_start(int(every))
     if st:
         raise WaveError(st, "wave_profile_start")
@@ -603,6 +608,32 @@ def wave_axpy(alpha: float, x: torch.Tensor, y: torch.Tensor, stream=None) -> to
     if st:
         raise WaveError(st, "wave_axpy")
     return y
+
+
+def wave_axpby(alpha: float, x: torch.Tensor, beta: float, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = alpha x + beta y in place (device float32 tensors of equal size)."""
+    if x.numel() != y.numel():
+        raise ValueError("x and y differ in size")
+    st = _lib().wave_axpby(y.numel(), float(alpha), _dev(x, "x"), float(beta), _dev(y, "y"), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_axpby")
+    return y
+
+
+DOT_PARTIALS = 256
+
+
+def wave_dot(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """sum x*y in double on the device, fixed order; returns a device float64
+    tensor whose element 0 holds the result (the rest is scratch)."""
+    if x.numel() != y.numel():
+        raise ValueError("x and y differ in size")
+    if out is None:
+        out = torch.empty(1 + DOT_PARTIALS, dtype=torch.float64, device=x.device)
+    st = _lib().wave_dot(x.numel(), _dev(x, "x"), _dev(y, "y"), ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_dot")
+    return out
 
 
 def wave_clamp(y: torch.Tensor, lo: float, hi: float, stream=None) -> torch.Tensor:

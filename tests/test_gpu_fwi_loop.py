@@ -101,22 +101,24 @@ def test_timelapse_batch_matches_oracle_per_vintage(store, tol):
     # vintage's misfit and gradient checked against the FP64 oracle on its own model and data
     import oracle
 
-    p, base, dv = _survey(nshot=3, nt=400)
-    acq = precond.Acquisition.of(p)
+    p, base, dv = _survey(nshot=3, nt=700)  # long enough for the plume's reflections to arrive
     vints = [base, base + 0.5 * dv, base + dv]
     models = [dev(v) for v in vints]
     og = oracle.Grid(2, p.nx, p.nz, p.h, p.dt, p.nt, p.nb, vref=p.vref)
     q32 = np.repeat(oracle.ricker(p.f0, p.dt, p.nt).astype(np.float32)[None, :, None], p.nshot, axis=0)
     q = q32.astype(np.float64)  # the same wavelet values on both sides, from the oracle
-    d_obs_h = [oracle.forward(og, v.astype(np.float64), p.src, q, p.rec) for v in
-               (base + 0.1 * dv, base + 0.6 * dv, base + 1.1 * dv)]
+    # each vintage's observed data come from a model 2 % faster with a stronger plume: a
+    # residual of a good fraction of the records (a residual of 1 % of them would be
+    # dominated by the FP32 rounding of the 700-step synthetic records, about 4e-5 of them)
+    d_obs_h = [oracle.forward(og, (1.02 * v + 0.5 * dv).astype(np.float64), p.src, q, p.rec) for v in vints]
     d_obs = [dev(d) for d in d_obs_h]
-    mb, gb = fwi.timelapse_gradients(acq.grid, models, p.src, p.rec, dev(q32), d_obs, store=store,
+    mb, gb = fwi.timelapse_gradients(wave.Grid.of(p), models, p.src, p.rec, dev(q32), d_obs, store=store,
                                      wrt=wave.WRT_SLOWNESS2, batched=True)
     errs = []
     for i, v in enumerate(vints):
         phi_ref, g_ref = oracle.gradient(og, v.astype(np.float64), p.src, q, p.rec, d_obs_h[i])
-        assert abs(mb[i] - phi_ref) <= 1e-4 * phi_ref, (i, mb[i], phi_ref)
+        # the misfit is quadratic in records that match to 1e-4 (as in the uneven-batch tests)
+        assert abs(mb[i] - phi_ref) <= 3e-4 * phi_ref, (i, mb[i], phi_ref)
         errs.append(rel(gb[i].cpu().numpy(), g_ref))
     print(f"time-lapse batch vs oracle, store {store}: gradient rel L2 per vintage {errs}")
     assert max(errs) < tol, errs
