@@ -41,6 +41,11 @@ VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,fwd>"),
                   (0, 27): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,fwd>"),
                   (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>"),
                   (1, 25): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,adj>")}
+# shot-group TMA kernels with deeper rings and the adjoint's forward level by TMA
+for _k, _fl, _g in ((39, 9, 2), (40, 9, 4), (41, 17, 4), (42, 9, 8), (43, 17, 8)):
+    VARIANT_KERNEL[(0, _k)] = ("k_step2d_sgt", "k_step2d_sgt<16,8,%d,%d,fwd>" % (_g, _fl))
+for _k, _fl, _g in ((37, 5, 2), (38, 13, 2), (39, 13, 4), (40, 5, 4)):
+    VARIANT_KERNEL[(1, _k)] = ("k_step2d_sgt", "k_step2d_sgt<16,8,%d,%d,adj>" % (_g, _fl))
 # the z-window kernels (step2d_zw.cu): (TZ, BZ, G) of forward variants 33-38 and adjoint variants 31-36
 for _i, _c in enumerate([(16, 4, 2), (16, 4, 4), (16, 2, 2), (32, 8, 2), (32, 4, 2), (16, 8, 2)]):
     for _which, _base, _tag in ((0, 33, "fwd"), (1, 31, "adj")):
@@ -226,18 +231,48 @@ def run_reference(args):
 
 
 def cpu_baseline(nt: int):
+    """The FP64 oracle on the host cores: one shot of the 32-shot gradient (the
+    headline sample), plus the survey's timing plan -- config 1 (full) at one
+    thread and at all cores, and config 2 at one thread on a shortened record
+    (nt = 400, scaled to the full record: the oracle's cost is linear in nt)."""
     import oracle
+    from paper_2304_05592_gb300 import synth
 
     oracle.build()
+    cores = oracle.threads()
+
+    def grad_time(p, vel, nt_run=None):
+        if nt_run:
+            p = p.with_nt(nt_run)
+        g = oracle.Grid(2, p.nx, p.nz, p.h, p.dt, p.nt, p.nb, vref=p.vref)
+        q = oracle.ricker(p.f0, p.dt, p.nt)[None, :, None]
+        src, rec = p.src[:1], p.rec[:1]
+        dobs = oracle.forward(g, p.vel, src, q, rec)
+        t = time.perf_counter()
+        oracle.gradient(g, vel, src, q, rec, dobs)
+        return time.perf_counter() - t, 2.0 * (p.nt - 1) * p.padded_points
+
     p, v0 = make_problem(1, nt)
-    g = oracle.Grid(2, p.nx, p.nz, p.h, p.dt, p.nt, p.nb, vref=p.vref)
-    q = oracle.ricker(p.f0, p.dt, p.nt)[None, :, None]
-    dobs = oracle.forward(g, p.vel, p.src, q, p.rec)
-    t = time.perf_counter()
-    oracle.gradient(g, v0, p.src, q, p.rec, dobs)
-    el = time.perf_counter() - t
-    return {"value": 1.0 / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"1 shot of the 32 (full grid, nt={nt}), one gradient, FP64, {el:.1f} s"}
+    el, _ = grad_time(p, v0)
+    out = {"value": 1.0 / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"1 shot of the 32 (full grid, nt={nt}), one gradient, FP64, {el:.1f} s"}
+    plan = {}
+    c1 = synth.config1()
+    v1 = (c1.vel * 1.03).astype(np.float32)
+    for th in (1, cores):
+        oracle.set_threads(th)
+        e, ups = grad_time(c1, v1)
+        plan[f"config1_gradient_{th}_threads"] = {"s": e, "pt_updates_per_s": ups / e, "shot_gradients_per_s": 1 / e}
+    oracle.set_threads(1)
+    e, ups = grad_time(p, v0, 400)
+    full = e * (nt - 1) / 399
+    plan["config2_gradient_1_thread"] = {"s_at_nt_400": e, "pt_updates_per_s": ups / e,
+                                         "shot_gradients_per_s_extrapolated": 1 / full}
+    oracle.set_threads(cores)
+    plan["config2_gradient_all_threads"] = {"s": el, "shot_gradients_per_s": 1 / el,
+                                            "pt_updates_per_s": 2.0 * (nt - 1) * p.padded_points / el}
+    out["plan"] = plan
+    return out
 
 
 def _variant3d(v: int) -> str:

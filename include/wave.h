@@ -257,6 +257,9 @@ wave_status_t wave_clamp(long long n, float lo, float hi, float* y, void* stream
  * null when n = 0, which gives out[0] = 0). */
 #define WAVE_DOT_PARTIALS 256
 wave_status_t wave_axpby(long long n, float alpha, const float* x, float beta, float* y, void* stream);
+/* y = x .* y elementwise (n device floats), e.g. a diagonal preconditioner
+ * applied to a gradient; stream-ordered. */
+wave_status_t wave_mul(long long n, const float* x, float* y, void* stream);
 wave_status_t wave_dot(long long n, const float* x, const float* y, double* out, void* stream);
 
 /* The bounded wait that the persistent batch sweep uses between tiles, run by

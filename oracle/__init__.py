@@ -77,6 +77,8 @@ def _load():
         lib.og_courant_limit.argtypes = [ctypes.c_int]
         lib.og_courant_limit.restype = ctypes.c_double
         lib.og_threads.restype = ctypes.c_int
+        lib.og_set_threads.argtypes = [ctypes.c_int]
+        lib.og_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -128,6 +130,11 @@ def _check(code: int, what: str):
 
 def threads() -> int:
     return int(_load().og_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls (timing only; results do not depend on it)."""
+    _load().og_set_threads(int(n))
 
 
 def courant_limit(ndim: int) -> float:

@@ -565,3 +565,13 @@ int og_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of later calls (n >= 1); used to time the oracle on one core and on all. */
+void og_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

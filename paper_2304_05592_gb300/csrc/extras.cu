@@ -132,6 +132,12 @@ __global__ void k_axpby(long long n, float alpha, const float* __restrict__ x, f
         y[i] = fmaf(alpha, x[i], beta * y[i]);
 }
 
+__global__ void k_mul(long long n, const float* __restrict__ x, float* __restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i] * y[i];
+}
+
 // Dot product in double: kDotBlocks partial sums over a fixed grid-stride
 // split, then one block adds them in block order (same bits on every run).
 constexpr int kDotBlocks = 256;
@@ -238,6 +244,15 @@ wave_status_t wave_axpby(long long n, float alpha, const float* x, float beta, f
     if (n == 0) return WAVE_OK;
     count_launch();
     k_axpby<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, alpha, x, beta, y);
+    return launched();
+}
+
+wave_status_t wave_mul(long long n, const float* x, float* y, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return WAVE_ERR_ARG;
+    if (n == 0) return WAVE_OK;
+    count_launch();
+    k_mul<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, x, y);
     return launched();
 }
 

@@ -151,7 +151,8 @@ constexpr int kTZc2 = 8;          // 2D tap-cell height: divides every 2D tile h
 // z-march (kind 3): one warp per TZ-row strip, R warps per CTA, prefetch
 // distance NST rows, shot groups fed by TMA (kind 4, fields as kind 2; NST bit
 // 0: the previous level's tile comes by TMA too, bit 1: the sponge factors sit
-// in shared memory instead of registers), or
+// in shared memory instead of registers, bit 2: the adjoint's forward level
+// comes by TMA too, bits 3 / 4: a 3- / 4-stage ring instead of 2), or
 // the persistent kernel over (tile, shot) items (kind 5, R = thread rows), or
 // the z-window kernel (kind 7, below).
 // With kinds 2 and 4 in the adjoint, the gradient buffer holds one

@@ -365,27 +365,35 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
 // ---------------------------------------------------------------------------
 // 2D step, shot groups fed by TMA.  As the shot-group kernel, but each shot's
 // (TZ+8) x 136 halo tile of u arrives by one TMA load (zero fill outside the
-// padded grid) into a two-stage ring: the load of shot i+1 is issued by one
-// thread while shot i is computed.  Row offsets, the model and the sponge
+// padded grid) into a ring of NS stages (2 by default, 3 or 4 with FL bits 8
+// or 16): one thread keeps the loads of the next NS - 1 shots in flight while
+// shot i is computed.  FL bit 1 adds the previous level's tile to a stage,
+// bit 4 (adjoint) the forward level u^k.  Row offsets, the model and the sponge
 // factors are set up once per CTA in 32-bit form, so the per-shot work is the
 // stencil arithmetic, one load of the previous level and one store per 4
 // points.  Waits on the ring are bounded; on a timeout the CTA records
 // kErrTimeout, lets its issued copies land and returns.
 template <int TZ, int BZ, int G, int FL, bool ADJ>
-__global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ)))
+__global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
+                                          : (FL & 8) ? 768 / (32 * BZ)
+                                          : (FL & 2) ? 1280 / (32 * BZ)
+                                          : ((TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ)))
     k_step2d_sgt(const __grid_constant__ StepMaps mp, const StepArgs a)
 {
     constexpr bool PT = (FL & 1) != 0;  // the previous level's tile comes by TMA
     constexpr bool SE = (FL & 2) != 0;  // sponge factors kept in shared memory, not registers
+    constexpr bool FT = ADJ && (FL & 4) != 0;  // adjoint: the forward level u^k comes by TMA too
+    constexpr int NS = (FL & 16) ? 4 : ((FL & 8) ? 3 : 2);  // ring stages: copies run NS - 1 shots ahead
     constexpr int SW = kTX + 8;
     constexpr int RB = TZ / BZ;
     constexpr int SU = (TZ + 8) * SW;          // halo tile of u
-    constexpr int SU2 = SU + (PT ? TZ * kTX : 0);  // one stage (+ the previous level's tile with PT)
+    constexpr int SP = PT ? TZ * kTX : 0;      // previous level's tile (PT)
+    constexpr int SU2 = SU + SP + (FT ? TZ * kTX : 0);  // one stage (+ u^k, FP32 or BF16 in the first half)
     static_assert(SU % 32 == 0 && SU2 % 32 == 0, "stages must stay 128-byte aligned");
     extern __shared__ unsigned char dyn[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[NS];
     float* st = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
-    float* sg = st + 2 * SU2;                         // [TZ][kTX] gradient tile (adjoint with imaging)
+    float* sg = st + NS * SU2;                        // [TZ][kTX] gradient tile (adjoint with imaging)
     float* se = sg + (ADJ ? TZ * kTX : 0);            // [2][TZ][kTX] eps and 1/(1+eps) (SE)
     const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
     const CUtensorMap* mt = ADJ ? &mp.tile_a : &mp.tile_f;
@@ -396,11 +404,23 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
     const int nvalid = min(4, a.Nx - gx);
     const bool imaging = ADJ && a.gacc != nullptr;
     const bool sparse = a.inj.cell_start != nullptr || a.gat.cell_start != nullptr;
-    constexpr uint32_t kBytes = SU2 * 4u;
+    const bool ft = FT && imaging && (a.uf16 ? a.uf16_row >= 0 : a.uf_buf >= 0);
+    const uint32_t kBytes = (uint32_t)(SU + SP) * 4u + (ft ? (uint32_t)(TZ * kTX) * (a.uf16 ? 2u : 4u) : 0u);
+    // copies of shot i into ring stage i % NS
+    auto issue = [&](int i) {
+        const int sj = i % NS;
+        float* sb = st + sj * SU2;
+        mbar_expect_tx(&bar[sj], kBytes);
+        tma_load_4d(sb, mh, &bar[sj], x0 - 4, z0 - 4, s0 + i, a.u_buf);
+        if (PT) tma_load_4d(sb + SU, mt, &bar[sj], x0, z0, s0 + i, a.prev_buf);
+        if (ft) {
+            if (a.uf16) tma_load_4d(sb + SU + SP, &mp.tile16_a, &bar[sj], x0, z0, s0 + i, a.uf16_row);
+            else tma_load_4d(sb + SU + SP, &mp.tile_a, &bar[sj], x0, z0, s0 + i, a.uf_buf);
+        }
+    };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int j = 0; j < NS; ++j) mbar_init(&bar[j], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -445,11 +465,8 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
         }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0) {
-        mbar_expect_tx(&bar[0], kBytes);
-        tma_load_4d(st, mh, &bar[0], x0 - 4, z0 - 4, s0, a.u_buf);
-        if (PT) tma_load_4d(st + SU, mt, &bar[0], x0, z0, s0, a.prev_buf);
-    }
+    if (tid == 0)
+        for (int j = 0; j < NS - 1 && j < ns; ++j) issue(j);
     float* gq = imaging ? a.gacc + (size_t)grp * a.cell : nullptr;
     if (imaging) {
 #pragma unroll
@@ -464,15 +481,13 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
     // A thread whose wait for a stage gives up records the timeout and does no
     // further work, but passes every block barrier below (they are uniform), so
     // the CTA never splits; thread 0, which issues the copies, first waits
-    // (bounded) for the two it has in flight and issues no more.
+    // (bounded) for the copies it has in flight and issues no more.
     bool alive = true;
     for (int i = 0; i < ns; ++i) {
-        const int shot = s0 + i, stage = i & 1;
-        if (tid == 0 && alive && i + 1 < ns) {
+        const int shot = s0 + i, stage = i % NS;
+        if (tid == 0 && alive && i + NS - 1 < ns) {
             fence_proxy_async();
-            mbar_expect_tx(&bar[stage ^ 1], kBytes);
-            tma_load_4d(st + (stage ^ 1) * SU2, mh, &bar[stage ^ 1], x0 - 4, z0 - 4, shot + 1, a.u_buf);
-            if (PT) tma_load_4d(st + (stage ^ 1) * SU2 + SU, mt, &bar[stage ^ 1], x0, z0, shot + 1, a.prev_buf);
+            issue(i + NS - 1);  // into the stage shot i - 1 used (released by the barrier after it)
         }
         const size_t so = (size_t)shot * a.cell;
         float4 uo[RB];
@@ -482,13 +497,12 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
                 uo[rr] = live[rr] ? *reinterpret_cast<const float4*>(a.uprev + so + off[rr])
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (alive && !mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u)) {
+        if (alive && !mbar_wait(&bar[stage], (uint32_t)(i / NS) & 1u)) {
             alive = false;
             atomicOr(a.err, kErrTimeout);
             if (tid == 0) {
                 // copies issued by this CTA may still land in its shared memory
-                mbar_wait(&bar[stage], (uint32_t)(i >> 1) & 1u);
-                if (i + 1 < ns) mbar_wait(&bar[stage ^ 1], (uint32_t)((i + 1) >> 1) & 1u);
+                for (int j = i; j < i + NS && j < ns; ++j) mbar_wait(&bar[j % NS], (uint32_t)(j / NS) & 1u);
             }
         }
         const float* sb = st + stage * SU2;
@@ -545,7 +559,17 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
                 }
             } else if (imaging) {
                 float uf[4];
-                if (a.uf16) {
+                if (ft && a.uf16) {
+                    unpack_bf16x4(*reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(sb + SU + SP) +
+                                                                  r * kTX + lx),
+                                  uf);
+                } else if (ft) {
+                    const float4 v = lds4(sb + SU + SP + r * kTX + lx);
+                    uf[0] = v.x;
+                    uf[1] = v.y;
+                    uf[2] = v.z;
+                    uf[3] = v.w;
+                } else if (a.uf16) {
                     unpack_bf16x4(*reinterpret_cast<const uint2*>(a.uf16 + so + off[rr]), uf);
                 } else {
                     const float4 v = ld4(a.uf32 + so + off[rr]);
@@ -576,8 +600,8 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 2) ? 1280 / (32 * BZ) : ((TZ / 
             }
         }
         const bool taps = ie > ib || ge > gb;
-        // the stage is refilled by shot i + 2's copies, and taps touch other threads' points
-        if (taps || i + 2 < ns) __syncthreads();
+        // the stage is refilled by shot i + NS's copies, and taps touch other threads' points
+        if (taps || i + NS < ns) __syncthreads();
         if (taps) {
             sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * BZ, imaging ? sg : nullptr, z0, x0);
             if (imaging) __syncthreads();  // injection terms land in the gradient tile before the next shot
@@ -1248,7 +1272,7 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
 // as centre: one barrier per plane.  Sponge depths in x and y are fixed per
 // thread.  Waits are bounded; on a timeout the CTA records kErrTimeout, lets
 // its issued copies land and returns.
-template <int TY, int TZC, int NR, bool ADJ>
+template <int TY, int TZC, int NR, bool ADJ, int PF = 0>
 __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const __grid_constant__ StepMaps mp,
                                                                         const StepArgs a)
 {
@@ -1272,6 +1296,20 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
     const size_t roff = (size_t)gy * a.P + gx;
     const bool imaging = ADJ && a.gacc != nullptr;
     constexpr uint32_t kBytes = SP * 4u;
+    // PF > 0: the model and the previous level of the thread's 4 points arrive
+    // PF planes ahead by cp.async into PF + 1 per-thread slots of shared memory
+    // ([slot][kap, uprev][thread] float4s: conflict-free), without registers
+    constexpr int NT = 32 * TY, PS = PF + 1;
+    float4* pre = reinterpret_cast<float4*>(ring + NR * SP);
+    auto prefetch = [&](int i) {  // plane z0 + i
+        const int gz = z0 + i;
+        if (PF > 0 && live && gz < z1) {
+            const int sl = i % PS;
+            cp_async16(pre + (2 * sl) * NT + tid, a.kap + gz * plane + roff, 16);
+            cp_async16(pre + (2 * sl + 1) * NT + tid, a.uprev + so + gz * plane + roff, 16);
+        }
+        if (PF > 0) cp_async_commit();
+    };
 
     auto issue = [&](int j) {
         const int sl = j % NR;
@@ -1283,6 +1321,7 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
     int issued = -1;  // highest plane index issued (thread 0)
     auto drain = [&](int from) {
         // copies issued by this CTA may still land in its shared memory
+        if (PF > 0) cp_async_wait_all();
         if (tid == 0) {
             atomicOr(a.err, kErrTimeout);
             for (int j = from; j <= issued; ++j) waitp(j);
@@ -1326,19 +1365,29 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
         q[j] = own(j);
     }
 
-    // the model and the previous level of the next plane are loaded one plane ahead
+    // the model and the previous level of the next plane are loaded one plane
+    // ahead (PF = 0), or PF planes ahead into shared memory
     float4 kp = make_float4(0.f, 0.f, 0.f, 0.f), uo = kp;
-    if (live) {
+    if (PF == 0 && live) {
         kp = ld4(a.kap + z0 * plane + roff);
         uo = *reinterpret_cast<const float4*>(a.uprev + so + z0 * plane + roff);
     }
+    for (int j = 0; j < PF; ++j) prefetch(j);
     for (int i = 0; i < z1 - z0; ++i) {
         const int gz = z0 + i;
         const size_t off = gz * plane + roff;
         float4 kpn = make_float4(0.f, 0.f, 0.f, 0.f), uon = kpn;
-        if (live && gz + 1 < z1) {
+        if (PF == 0 && live && gz + 1 < z1) {
             kpn = ld4(a.kap + off + plane);
             uon = *reinterpret_cast<const float4*>(a.uprev + so + off + plane);
+        }
+        if (PF > 0) {
+            prefetch(i + PF);    // into the slot plane i - 1 used
+            cp_async_wait<PF>();  // plane i's copies (PF groups younger than it may stay pending)
+            if (live) {
+                kp = pre[(2 * (i % PS)) * NT + tid];
+                uo = pre[(2 * (i % PS) + 1) * NT + tid];
+            }
         }
         ok = waitp(i + 8) && ok;
         q[8] = own(i + 8);
@@ -1385,8 +1434,10 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
-        kp = kpn;
-        uo = uon;
+        if (PF == 0) {
+            kp = kpn;
+            uo = uon;
+        }
         // every thread is done with the centre slot of this plane: refill it
         if (__syncthreads_or(!ok)) {
             drain(0);
@@ -1663,7 +1714,8 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {5, 16, 8, 0, 0}, {5, 8, 8, 0, 0}, {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2},
                                    {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}, {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2},
                                    {4, 16, 8, 2, 4},  {7, 16, 4, 0, 2}, {7, 16, 4, 1, 4}, {7, 16, 2, 2, 2},
-                                   {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2}, {7, 16, 8, 5, 2}};
+                                   {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2}, {7, 16, 8, 5, 2}, {4, 16, 8, 9, 2},
+                                   {4, 16, 8, 9, 4},  {4, 16, 8, 17, 4}, {4, 16, 8, 9, 8}, {4, 16, 8, 17, 8}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
@@ -1673,13 +1725,16 @@ static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2
                                    {5, 32, 8, 0, 0}, {4, 16, 8, 1, 2}, {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4},
                                    {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2}, {4, 16, 8, 2, 4},  {7, 16, 4, 0, 2},
                                    {7, 16, 4, 1, 4}, {7, 16, 2, 2, 2}, {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2},
-                                   {7, 16, 8, 5, 2}};
+                                   {7, 16, 8, 5, 2}, {4, 16, 8, 5, 2}, {4, 16, 8, 13, 2}, {4, 16, 8, 13, 4},
+                                   {4, 16, 8, 5, 4}};
 // 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y, NST = ring
-// slots, G = 1 for the ring without block barriers): kind 0 is the z-march
-// with a shared-memory halo plane, kind 6 the TMA plane ring.
+// slots, G = 1 for the ring without block barriers, G = PF + 1 for the ring
+// whose model and previous level arrive PF planes ahead by cp.async): kind 0
+// is the z-march with a shared-memory halo plane, kind 6 the TMA plane ring.
 static const Variant2D k3D[] = {{0, 32, 8, 0, 0},  {6, 32, 8, 7, 0},  {6, 64, 8, 7, 0},  {6, 32, 16, 7, 0},
                                 {6, 64, 16, 7, 0}, {6, 64, 8, 10, 0}, {6, 32, 8, 10, 0}, {6, 96, 8, 10, 0},
-                                {6, 64, 8, 10, 1}, {6, 64, 8, 12, 1}, {6, 96, 8, 12, 1}};
+                                {6, 64, 8, 10, 1}, {6, 64, 8, 12, 1}, {6, 96, 8, 12, 1}, {6, 64, 8, 8, 4},
+                                {6, 64, 8, 7, 5},  {6, 96, 8, 8, 4}};
 static int g_selected[3] = {-1, -1, -1};
 static const int kDefaultVariant[3] = {18, 16, 5};
 
@@ -1729,20 +1784,22 @@ static void launch_3d_ws(bool adjoint, const StepArgs& a, const StepMaps* maps, 
     else k_step3d_ws<TY, TZC, NR, false><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
 }
 
-template <int TY, int TZC, int NR>
+template <int TY, int TZC, int NR, int PF = 0>
 static void launch_3d_tma(bool adjoint, const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
-    constexpr size_t smem = (size_t)NR * (TY + 8) * (kTX + 8) * 4 + 128;
+    constexpr size_t smem = (size_t)NR * (TY + 8) * (kTX + 8) * 4 + (size_t)(PF > 0 ? (PF + 1) * 2 * 32 * TY * 16 : 0) +
+                            128;
     static bool configured[kMaxDev] = {};
     if (first_on_device(configured)) {
-        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, false, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step3d_tma<TY, TZC, NR, true, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     }
     const int ntz = (a.Nz + TZC - 1) / TZC;
     dim3 grid(a.ncx, (a.Ny + TY - 1) / TY, ntz * a.nshot);
-    if (adjoint) k_step3d_tma<TY, TZC, NR, true><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
-    else k_step3d_tma<TY, TZC, NR, false><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+    if (adjoint) k_step3d_tma<TY, TZC, NR, true, PF><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
+    else k_step3d_tma<TY, TZC, NR, false, PF><<<grid, dim3(32, TY), smem, s>>>(*maps, a);
 }
 
 template <int TZ, int BZ, int G, bool ADJ>
@@ -1760,8 +1817,10 @@ static void launch_2d_group(const StepArgs& a, cudaStream_t s)
 template <int TZ, int BZ, int G, bool ADJ, int FL = 0>
 static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStream_t s)
 {
-    constexpr size_t smem = (size_t)(2 * ((TZ + 8) * (kTX + 8) + ((FL & 1) ? TZ * kTX : 0)) + (ADJ ? TZ * kTX : 0) +
-                                     ((FL & 2) ? 2 * TZ * kTX : 0)) * 4 + 128;
+    constexpr int NS = (FL & 16) ? 4 : ((FL & 8) ? 3 : 2);
+    constexpr size_t smem = (size_t)(NS * ((TZ + 8) * (kTX + 8) + ((FL & 1) ? TZ * kTX : 0) +
+                                           ((ADJ && (FL & 4)) ? TZ * kTX : 0)) +
+                                     (ADJ ? TZ * kTX : 0) + ((FL & 2) ? 2 * TZ * kTX : 0)) * 4 + 128;
     static bool configured[kMaxDev] = {};
     if (first_on_device(configured)) {
         cudaFuncSetAttribute(k_step2d_sgt<TZ, BZ, G, FL, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1891,6 +1950,11 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 30: launch_2d_group_tma<16, 8, 2, false, 2>(a, maps, s); break;
             case 31: launch_2d_group_tma<16, 8, 2, false, 3>(a, maps, s); break;
             case 32: launch_2d_group_tma<16, 8, 4, false, 2>(a, maps, s); break;
+            case 39: launch_2d_group_tma<16, 8, 2, false, 9>(a, maps, s); break;
+            case 40: launch_2d_group_tma<16, 8, 4, false, 9>(a, maps, s); break;
+            case 41: launch_2d_group_tma<16, 8, 4, false, 17>(a, maps, s); break;
+            case 42: launch_2d_group_tma<16, 8, 8, false, 9>(a, maps, s); break;
+            case 43: launch_2d_group_tma<16, 8, 8, false, 17>(a, maps, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -1925,6 +1989,10 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 28: launch_2d_group_tma<16, 8, 2, true, 2>(a, maps, s); break;
             case 29: launch_2d_group_tma<16, 8, 2, true, 3>(a, maps, s); break;
             case 30: launch_2d_group_tma<16, 8, 4, true, 2>(a, maps, s); break;
+            case 37: launch_2d_group_tma<16, 8, 2, true, 5>(a, maps, s); break;
+            case 38: launch_2d_group_tma<16, 8, 2, true, 13>(a, maps, s); break;
+            case 39: launch_2d_group_tma<16, 8, 4, true, 13>(a, maps, s); break;
+            case 40: launch_2d_group_tma<16, 8, 4, true, 5>(a, maps, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }
@@ -1940,6 +2008,9 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
         case 8: launch_3d_ws<8, 64, 10>(adjoint, a, maps, s); break;
         case 9: launch_3d_ws<8, 64, 12>(adjoint, a, maps, s); break;
         case 10: launch_3d_ws<8, 96, 12>(adjoint, a, maps, s); break;
+        case 11: launch_3d_tma<8, 64, 8, 3>(adjoint, a, maps, s); break;
+        case 12: launch_3d_tma<8, 64, 7, 4>(adjoint, a, maps, s); break;
+        case 13: launch_3d_tma<8, 96, 8, 3>(adjoint, a, maps, s); break;
         default: {
             const int ntz = (a.Nz + 31) / 32;
             dim3 grid(t.ncx, t.ncy, ntz * a.nshot);

@@ -4,7 +4,7 @@
   drawn at random with replacement, which is how the paper keeps the count of
   wave-equation solves down (arxiv 2304.05592, section "Putting it all together":
   four random shots per iteration, 200 iterations, about 25 passes through the
-  data); the step along the subset gradient is found by backtracking on the
+  data); the step along the subset gradient is found by a line search on the
   subset misfit, and models stay within velocity bounds.
 * ``timelapse_gradients``: the block-diagonal time-lapse operator
   F(v) = diag(F^i(v^i) q^i) of the same section: each vintage has its own
@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import wave
-from .precond import Acquisition, Misfit
+from .precond import Acquisition, Misfit, line_search
 from .wave import BatchProblem
 
 
@@ -31,7 +31,7 @@ from .wave import BatchProblem
 class FWIHistory:
     shots: list = field(default_factory=list)        # shot indices of each iteration
     subset_misfit: list = field(default_factory=list)
-    step: list = field(default_factory=list)         # accepted step (m/s at the largest cell), 0 = none
+    step: list = field(default_factory=list)         # accepted step (m/s RMS over the grid), 0 = none
     full_misfit: list = field(default_factory=list)  # (iteration, misfit over all shots)
     solves: int = 0
 
@@ -59,18 +59,7 @@ def fwi_subsampled(acq: Acquisition, d_obs: torch.Tensor, v0: torch.Tensor, iter
         sub, dsub = _subset(acq, d_obs, shots)
         M = Misfit(sub, dsub)
         phi, g = M.gradient(v)
-        gmax = float(g.abs().max().clamp_min(1e-30))
-        a = first_len / gmax
-        taken = 0.0
-        for _ in range(6):
-            cand = v.clone()
-            wave.wave_axpy(-a, g, cand)
-            wave.wave_clamp(cand, vmin, vmax)
-            pc = M.value(cand)
-            if pc < phi:
-                v, phi, taken = cand, pc, a * gmax
-                break
-            a *= 0.5
+        v, phi, taken, _ = line_search(M, v, phi, g, first_len, vmin, vmax)
         h.shots.append(shots.tolist())
         h.subset_misfit.append(phi)
         h.step.append(taken)

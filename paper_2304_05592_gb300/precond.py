@@ -11,9 +11,10 @@ Pieces (every wave solve and every network step runs in libwave's kernels):
 * ``train``: Adam on the mean squared error over shuffled mini-batches.
 * ``fwi``: gradient-descent FWI where each iteration either takes the FNO
   update (accepted only if the data misfit drops, tried at full and half
-  length) or falls back to the plain gradient step with a backtracking line
-  search; the plain solver's misfit judges every update.  With ``net=None`` it
-  is the plain method.
+  length) or falls back to the plain step: the depth-weighted gradient
+  (``depth_weights``) with a safeguarded quadratic line search
+  (``line_search``); the plain solver's misfit judges every update.  With
+  ``net=None`` it is the plain method.
 
 The paper runs FWI with stochastic shot subsampling and learned components
 (arxiv 2304.05592, sections "Wave-equation-based inversion" and "Fourier neural
@@ -71,12 +72,15 @@ class Misfit:
 
 
 def features(g: torch.Tensor) -> torch.Tensor:
-    """Network input [1][3][nz][nx]: gradient / RMS(gradient), z and x in [0, 1]."""
+    """Network input [1][3][nz][nx]: gradient / RMS(gradient) (scaled by a
+    libwave kernel), z and x in [0, 1]."""
     nz, nx = g.shape
-    rms = torch.sqrt(torch.mean(g.double() ** 2)).float().clamp_min(1e-30)
-    z = torch.linspace(0, 1, nz, device=g.device)[:, None].expand(nz, nx)
-    x = torch.linspace(0, 1, nx, device=g.device)[None, :].expand(nz, nx)
-    return torch.stack([g / rms, z, x])[None].contiguous()
+    out = torch.zeros((1, 3, nz, nx), dtype=torch.float32, device=g.device)
+    rms = max((_dot(g, g) / g.numel()) ** 0.5, 1e-30)
+    wave.wave_axpy(1.0 / rms, g.contiguous(), out[0, 0])
+    out[0, 1] = torch.linspace(0, 1, nz, device=g.device)[:, None]
+    out[0, 2] = torch.linspace(0, 1, nx, device=g.device)[None, :]
+    return out
 
 
 def make_pairs(seeds, acq: Acquisition, model=synth.plume_model, device="cuda", log=None):
@@ -118,38 +122,99 @@ def train(net: fno.FNO2d, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch: 
     return hist
 
 
-def plain_step(M: Misfit, v, phi, g, first_len: float = 50.0, vmin=1400.0, vmax=5000.0):
-    """Gradient step with a backtracking line search: the first trial moves
-    the largest cell by first_len m/s, halved up to 5 times; returns the new
-    model and misfit (the old ones if nothing reduced the misfit)."""
-    a = first_len / float(g.abs().max().clamp_min(1e-30))
-    for _ in range(6):
-        cand = (v - a * g).clamp(vmin, vmax)
-        pc = M.value(cand)
-        if pc < phi:
-            return cand, pc, "plain"
-        a *= 0.5
-    return v, phi, "none"
+def _dot(x: torch.Tensor, y: torch.Tensor) -> float:
+    return float(wave.wave_dot(x, y)[0].item())
 
 
-def fwi(M: Misfit, v0: torch.Tensor, iters: int, net: fno.FNO2d = None, vmin=1400.0, vmax=5000.0):
-    """FWI from v0; returns misfits after 0..iters iterations and the step kinds."""
+def _trial(M: Misfit, v: torch.Tensor, a: float, d: torch.Tensor, vmin: float, vmax: float):
+    """The model v + a d clamped to [vmin, vmax] (libwave kernels) and its misfit."""
+    cand = v.clone()
+    wave.wave_axpy(a, d, cand)
+    wave.wave_clamp(cand, vmin, vmax)
+    return cand, M.value(cand)
+
+
+def depth_weights(nz: int, nx: int, device="cuda") -> torch.Tensor:
+    """Depth preconditioner of the velocity gradient, w(z) = (z + 1) / nz: the
+    standard compensation for the geometric spreading that makes the gradient
+    of a surface survey decay with depth (an input table, built once)."""
+    w = (torch.arange(nz, dtype=torch.float32, device=device) + 1.0) / nz
+    return w[:, None].expand(nz, nx).contiguous()
+
+
+def line_search(M: Misfit, v: torch.Tensor, phi: float, g: torch.Tensor, first_len: float = 50.0,
+                vmin: float = 1400.0, vmax: float = 5000.0, max_evals: int = 6, weights: torch.Tensor = None):
+    """Step along d = -g (or -w .* g with diagonal weights w) with a
+    safeguarded quadratic line search on the misfit (interpolation as in
+    Nocedal and Wright, ch. 3).  The first trial is the step that would zero
+    a misfit falling linearly at slope <g, d>, a = phi / |<g, d>|, kept
+    between 1 m/s and 4 first_len m/s in RMS over the grid (so neither a
+    gradient that peaks at a few cells next to the sources nor a tiny
+    residual sets its scale); the parabola through phi(0), the slope and
+    phi(a) gives the next trial -- beyond a after a decrease (at most 4 a),
+    within [0.1 a, 0.5 a] after an increase -- and at most max_evals misfits
+    are evaluated.  Returns (model, misfit, step length in m/s RMS,
+    evaluations); the old model and 0 if no trial reduced the misfit."""
+    p = g if weights is None else wave.wave_mul(weights, g.clone())  # search along -p
+    gp = _dot(g, p)
+    if not gp > 0.0:
+        return v, phi, 0.0, 0
+    rms = (_dot(p, p) / p.numel()) ** 0.5
+    slope = -gp
+    a = min(max(phi / gp, 1.0 / rms), 4.0 * first_len / rms)
+    best_v, best_phi, best_a = v, phi, 0.0
+    cand, pa = _trial(M, v, -a, p, vmin, vmax)
+    evals = 1
+    if pa < phi:
+        best_v, best_phi, best_a = cand, pa, a
+    while evals < max_evals:
+        curv = pa - phi - slope * a
+        aq = -slope * a * a / (2.0 * curv) if curv > 0.0 else 4.0 * a
+        if best_a > 0.0:
+            # a decrease at a: one more trial at the parabola's minimum (or further out)
+            nxt = min(max(aq, 0.1 * a), 4.0 * a)
+            if abs(nxt - a) < 0.05 * a:
+                break
+            cand, pn = _trial(M, v, -nxt, p, vmin, vmax)
+            evals += 1
+            if pn < best_phi:
+                best_v, best_phi, best_a = cand, pn, nxt
+            break
+        a = min(max(aq, 0.1 * a), 0.5 * a)
+        cand, pa = _trial(M, v, -a, p, vmin, vmax)
+        evals += 1
+        if pa < phi:
+            best_v, best_phi, best_a = cand, pa, a
+    return best_v, best_phi, best_a * rms, evals
+
+
+def plain_step(M: Misfit, v, phi, g, first_len: float = 50.0, vmin=1400.0, vmax=5000.0, weights=None):
+    """The plain method's update: the line search along the (depth-weighted)
+    negative gradient; returns the new model, its misfit and "plain" (or the
+    old ones and "none" if no trial reduced the misfit)."""
+    nv, nphi, step, _ = line_search(M, v, phi, g, first_len, vmin, vmax, weights=weights)
+    return nv, nphi, ("plain" if step > 0.0 else "none")
+
+
+def fwi(M: Misfit, v0: torch.Tensor, iters: int, net: fno.FNO2d = None, vmin=1400.0, vmax=5000.0, weights=None):
+    """FWI from v0; returns misfits after 0..iters iterations and the step
+    kinds.  weights: diagonal preconditioner of the plain step (None: the
+    raw gradient)."""
     v = v0.clone()
     phi, g = M.gradient(v)
     hist, kinds = [phi], []
     for _ in range(iters):
         done = False
         if net is not None:
-            upd = net.forward(features(g), train=False)[0, 0] * SCALE
+            upd = net.forward(features(g), train=False)[0, 0].contiguous()
             for a in (1.0, 0.5):
-                cand = (v + a * upd).clamp(vmin, vmax)
-                pc = M.value(cand)
+                cand, pc = _trial(M, v, a * SCALE, upd, vmin, vmax)
                 if pc < phi:
                     v, phi, done = cand, pc, True
                     kinds.append("fno" if a == 1.0 else "fno/2")
                     break
         if not done:
-            v, phi, kind = plain_step(M, v, phi, g, vmin=vmin, vmax=vmax)
+            v, phi, kind = plain_step(M, v, phi, g, vmin=vmin, vmax=vmax, weights=weights)
             kinds.append(kind)
         hist.append(phi)
         # keep phi as evaluated for the accepted model (the gradient call's own
@@ -158,20 +223,36 @@ def fwi(M: Misfit, v0: torch.Tensor, iters: int, net: fno.FNO2d = None, vmin=140
     return hist, kinds, v
 
 
-def evaluate(seeds, acq: Acquisition, net: fno.FNO2d, iters: int, model=synth.plume_model, device="cuda"):
+# A model whose plume changes the records by less than this fraction of their
+# energy carries no plume signal within the record (the reflection arrives
+# after it ends): its residual is FP32 rounding, and it is left out of the
+# FWI comparison.
+MIN_SIGNAL = 1e-9
+
+
+def evaluate(seeds, acq: Acquisition, net: fno.FNO2d, iters: int, model=synth.plume_model, device="cuda",
+             depth_weighting: bool = True):
     """Misfit and model error after each iteration, plain vs preconditioned,
-    on held-out model seeds (both normalised by the starting values)."""
+    on held-out model seeds (both normalised by the starting values).  The
+    plain method (and the FNO runs' fallback) steps along the depth-weighted
+    gradient unless depth_weighting is off.  Seeds whose plume leaves no
+    signal in the records (MIN_SIGNAL) are listed in "no_signal" and skipped."""
     g0 = acq.grid
-    out = {"plain": [], "fno": [], "err_plain": [], "err_fno": [], "kinds": []}
+    W = depth_weights(g0.nz, g0.nx, device) if depth_weighting else None
+    out = {"plain": [], "fno": [], "err_plain": [], "err_fno": [], "kinds": [], "kinds_plain": [], "no_signal": []}
     for s in seeds:
         base, dv = model(int(s), nx=g0.nx, nz=g0.nz, h=g0.h)
         vb = torch.from_numpy(base).to(device)
         vt = torch.from_numpy(base + dv).to(device)
         d_obs = wave.wave_forward(g0, vt, acq.src, acq.wavelet, acq.rec)
         M = Misfit(acq, d_obs)
+        if M.value(vb) < MIN_SIGNAL * 0.5 * _dot(d_obs, d_obs):
+            out["no_signal"].append(int(s))
+            continue
         e0 = float(torch.linalg.vector_norm(vb - vt))
-        hp, _, vp = fwi(M, vb, iters)
-        hf, kinds, vf = fwi(M, vb, iters, net)
+        hp, kinds_p, vp = fwi(M, vb, iters, weights=W)
+        hf, kinds, vf = fwi(M, vb, iters, net, weights=W)
+        out["kinds_plain"].append(kinds_p)
         out["plain"].append(np.array(hp) / hp[0])
         out["fno"].append(np.array(hf) / hf[0])
         out["err_plain"].append(float(torch.linalg.vector_norm(vp - vt)) / e0)
@@ -223,13 +304,17 @@ def run(npairs: int = 2000, nheld: int = 200, nfwi: int = 32, iters: int = 3, ep
     t = time.perf_counter()
     ev = evaluate(range(ntr, ntr + nfwi), acq, net, iters, device=dev)
     res["fwi_s"] = time.perf_counter() - t
-    res["fwi_models"] = nfwi
+    res["fwi_models"] = nfwi - len(ev["no_signal"])
+    res["fwi_models_without_plume_signal"] = ev["no_signal"]
     res["misfit_plain"] = np.mean(ev["plain"], axis=0).tolist()
     res["misfit_fno"] = np.mean(ev["fno"], axis=0).tolist()
     res["model_error_plain"] = float(np.mean(ev["err_plain"]))
     res["model_error_fno"] = float(np.mean(ev["err_fno"]))
     kinds = [k for ks in ev["kinds"] for k in ks]
     res["step_kinds"] = {k: kinds.count(k) for k in sorted(set(kinds))}
+    kp = [k for ks in ev["kinds_plain"] for k in ks]
+    res["step_kinds_plain"] = {k: kp.count(k) for k in sorted(set(kp))}
+    res["plain_descent_rate"] = kp.count("plain") / max(len(kp), 1)
     return res
 
 

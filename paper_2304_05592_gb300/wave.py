@@ -128,6 +128,8 @@ def _lib():
         lib.wave_clamp.restype = I
         lib.wave_axpby.argtypes = [L, F, P, F, P, P]
         lib.wave_axpby.restype = I
+        lib.wave_mul.argtypes = [L, P, P, P]
+        lib.wave_mul.restype = I
         lib.wave_dot.argtypes = [L, P, P, P, P]
         lib.wave_dot.restype = I
         lib.wave_wait_probe.argtypes = [P, I, P, P, P]
@@ -617,6 +619,16 @@ def wave_axpby(alpha: float, x: torch.Tensor, beta: float, y: torch.Tensor, stre
     st = _lib().wave_axpby(y.numel(), float(alpha), _dev(x, "x"), float(beta), _dev(y, "y"), _stream(stream))
     if st:
         raise WaveError(st, "wave_axpby")
+    return y
+
+
+def wave_mul(x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = x .* y in place (device float32 tensors of equal size)."""
+    if x.numel() != y.numel():
+        raise ValueError("x and y differ in size")
+    st = _lib().wave_mul(y.numel(), _dev(x, "x"), _dev(y, "y"), _stream(stream))
+    if st:
+        raise WaveError(st, "wave_mul")
     return y
 
 

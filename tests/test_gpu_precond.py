@@ -1,8 +1,9 @@
 """The learned preconditioner gains over the plain method: an FNO trained on
 (RTM gradient, true perturbation) pairs that the plain solver generates, on
 plume models the network has not seen, lowers the data misfit and the model
-error after FWI iterations more than the plain gradient step with a line
-search does; every FNO update was accepted by the plain solver's misfit."""
+error after FWI iterations more than the plain method (depth-weighted
+gradient with a quadratic line search, which finds descent on nearly every
+iteration) does; every FNO update was accepted by the plain solver's misfit."""
 import numpy as np
 import pytest
 import torch
@@ -28,7 +29,11 @@ def test_fno_preconditioned_fwi_beats_plain_gradient_steps():
     assert hist[-1] < 0.5 * hist[0]
     ev = precond.evaluate(range(10000, 10008), acq, net, iters=2)
     plain, pre = np.mean(ev["plain"], axis=0), np.mean(ev["fno"], axis=0)
-    # measured: misfit 0.94 -> 0.49 after one iteration, model error 0.99 -> 0.58
+    kp = [k for ks in ev["kinds_plain"] for k in ks]
+    print(f"misfit plain {plain}, FNO {pre}; model error plain {np.mean(ev['err_plain']):.3f}, "
+          f"FNO {np.mean(ev['err_fno']):.3f}; plain steps accepted {kp.count('plain')}/{len(kp)}")
+    # the plain method (depth-weighted gradient, quadratic line search) finds descent
+    assert kp.count("plain") >= 0.9 * len(kp), kp
     assert pre[1] < 0.75 * plain[1], (plain, pre)
     assert pre[2] < 0.75 * plain[2], (plain, pre)
     assert np.mean(ev["err_fno"]) < 0.85 * np.mean(ev["err_plain"])
