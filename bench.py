@@ -34,9 +34,10 @@ WORKLOAD = ("2D FWI gradient, 32 shots: 512x256 at 6.25 m, layered 1500-3500 m/s
             "perturbation (100 m), 512 receivers, 20 Hz Ricker, nt=4000 at dt=0.5 ms, 40-cell sponge, FP32, "
             "binomial checkpointing")
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
-# (kernel, SHA-256 prefix of that kernel's source text plus the shared stencil header) at capture
-# time; a kernel whose source has changed since gets null.
+# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, caches
+# flushed before the launch, so the reads are cold and the dirty lines a launch leaves in L2 are not
+# counted), keyed by (kernel, SHA-256 prefix of that kernel's source text plus the shared stencil
+# header) at capture time; a kernel whose source has changed since gets null.
 VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,fwd>"),
                   (0, 27): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,fwd>"),
                   (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>"),
@@ -51,11 +52,10 @@ for _i, _c in enumerate([(16, 4, 2), (16, 4, 4), (16, 2, 2), (32, 8, 2), (32, 4,
     for _which, _base, _tag in ((0, 33, "fwd"), (1, 31, "adj")):
         VARIANT_KERNEL[(_which, _base + _i)] = ("k_step2d_zw", "k_step2d_zw<%d,%d,%d,%s>" % (*_c, _tag),
                                                 "step2d_zw.cu")
-TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "b1aa5bc1b5bee470"): 81.70e6,
-           ("k_step2d_sgt<16,8,2,1,fwd>", "b1aa5bc1b5bee470"): 81.73e6,
-           ("k_step2d_sgt<16,8,2,0,adj>", "b1aa5bc1b5bee470"): 93.41e6,
-           ("k_step2d_sgt<16,8,2,1,adj>", "b1aa5bc1b5bee470"): 93.96e6,
-           ("k_step3d_tma<8,64,10,fwd>", "ff84bd7b5179962b"): 1434.45e6}
+TRAFFIC = {("k_step2d_sgt<16,8,2,1,fwd>", "2badfa07c7efa163"): 53.42e6,
+           ("k_step2d_sgt<16,8,2,1,adj>", "2badfa07c7efa163"): 95.74e6,
+           ("k_step2d_sgt<16,8,4,5,adj>", "2badfa07c7efa163"): 87.00e6,
+           ("k_step3d_tma<8,64,10,fwd>", "edf5911651f90434"): 1385.46e6}
 
 
 def parse():

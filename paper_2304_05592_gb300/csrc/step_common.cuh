@@ -21,9 +21,11 @@ __device__ __forceinline__ int sponge_depth(int i, int nb, int n)
 // sgt, if given, is the tile's gradient accumulator in shared memory, with
 // its first point at (z0, x0).  WARP: the caller is one warp that owns the
 // tile (warp barrier instead of a block barrier).
-template <bool ADJ, bool WARP = false>
-__device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, int gb, int ge, long long so, int tid,
-                                             int nthr, float* sgt = nullptr, int z0 = 0, int x0 = 0)
+// bar() synchronises the nthr threads that run it (the version below uses the
+// block barrier, or the warp barrier with WARP).
+template <bool ADJ, class Bar>
+__device__ __forceinline__ void sparse_phase_bar(const StepArgs& a, int ib, int ie, int gb, int ge, long long so,
+                                                 int tid, int nthr, float* sgt, int z0, int x0, Bar bar)
 {
     float* un = a.unew + so;
     if (a.inj.cell_start) {
@@ -59,11 +61,20 @@ __device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, 
         }
     }
     if (a.gat.cell_start) {
-        if (WARP) __syncwarp();
-        else __syncthreads();
+        bar();
         float* row = a.slots + (long long)a.slot_row * a.gat.ntap;
         for (int j = gb + tid; j < ge; j += nthr) row[a.gat.slot[j]] = a.gat.gw[j] * un[a.gat.idx[j]];
     }
+}
+
+template <bool ADJ, bool WARP = false>
+__device__ __forceinline__ void sparse_phase(const StepArgs& a, int ib, int ie, int gb, int ge, long long so, int tid,
+                                             int nthr, float* sgt = nullptr, int z0 = 0, int x0 = 0)
+{
+    sparse_phase_bar<ADJ>(a, ib, ie, gb, ge, so, tid, nthr, sgt, z0, x0, [] {
+        if (WARP) __syncwarp();
+        else __syncthreads();
+    });
 }
 
 }  // namespace wave
