@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--nsnap", type=int, default=256, help="checkpoint slots (two FP32 fields per shot each)")
+    ap.add_argument("--nsnap", type=int, default=1536,
+                    help="checkpoint slots (two FP32 fields per shot each; 1536 = 80 GB for the 32-shot survey)")
     ap.add_argument("--nshot", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
     ap.add_argument("--only-main", action="store_true", help="timed gradient steps only (for launch lists)")
@@ -458,16 +459,16 @@ def lsrtm_config2(dev, iters: int = 2):
     dm = 0.03 * m0 * (np.exp(-((zz - 120) ** 2 + (xx - 200) ** 2) / 200.0)
                       - np.exp(-((zz - 180) ** 2 + (xx - 330) ** 2) / 150.0))
     dd = wave.wave_born(g, vel, p.src, q, p.rec, torch.from_numpy(dm.astype(np.float32)).to(dev))
-    lsrtm.lsrtm_cgls(g, vel, p.src, q, p.rec, dd, 1, nsnap=256)  # warm-up
+    lsrtm.lsrtm_cgls(g, vel, p.src, q, p.rec, dd, 1, nsnap=1536)  # warm-up
     torch.cuda.synchronize()
     t = time.perf_counter()
-    _, hist = lsrtm.lsrtm_cgls(g, vel, p.src, q, p.rec, dd, iters, nsnap=256)
+    _, hist = lsrtm.lsrtm_cgls(g, vel, p.src, q, p.rec, dd, iters, nsnap=1536)
     torch.cuda.synchronize()
     el = time.perf_counter() - t
     return {"workload": "LSRTM (CGLS) on the 32-shot config-2 survey, Born data of a known perturbation",
             "iterations_per_s": iters / el, "iterations_timed": iters,
             "residual_ratio": hist.rnorm[-1] / hist.rnorm[0],
-            "per_iteration": "1 wave_born + 1 wave_jacobian_adjoint (checkpointed, 256 slots) + 3 dot products"}
+            "per_iteration": "1 wave_born + 1 wave_jacobian_adjoint (checkpointed, 1536 slots) + 3 dot products"}
 
 
 def main():
