@@ -77,7 +77,8 @@ struct BVariant {
 };
 // (Stages of the adjoint sweep hold five arrays: 45.8 KB at TZ = 16, 87.3 KB at TZ = 32.)
 const BVariant kBatchVariants[] = {{0, 32, 8, 0, 0},  {1, 16, 4, 2, 0}, {1, 16, 4, 3, 0}, {1, 32, 8, 2, 0},
-                                   {1, 32, 4, 2, 0},  {1, 16, 2, 3, 0}, {1, 16, 8, 2, 0}, {1, 16, 4, 2, 2}};
+                                   {1, 32, 4, 2, 0},  {1, 16, 2, 3, 0}, {1, 16, 8, 2, 0}, {1, 16, 4, 2, 2},
+                                   {1, 16, 8, 3, 0},  {1, 16, 2, 2, 0}, {1, 16, 8, 2, 1}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 constexpr int kDefaultBatchVariant = 1;
 constexpr int kMinTZ = 16;  // smallest tile height of any variant (sizes the tile tables)
@@ -996,6 +997,8 @@ wave_status_t launch_sweep(const BatchLayout& B, int variant, bool adj, int nste
     SWEEP(32, 4, 2)
     SWEEP(16, 2, 3)
     SWEEP(16, 8, 2)
+    SWEEP(16, 8, 3)
+    SWEEP(16, 2, 2)
 #undef SWEEP
     return WAVE_ERR_ARG;
 }

@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
     static_assert(SU % 32 == 0 && SU2 % 32 == 0, "stages must stay 128-byte aligned");
     extern __shared__ unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar[NS];
+    __shared__ int taprng[G][4];  // per shot of the group: injection and gather tap ranges
     float* st = reinterpret_cast<float*>(dyn + ((128u - (smem_u32(dyn) & 127u)) & 127u));
     float* sg = st + NS * SU2;                        // [TZ][kTX] gradient tile (adjoint with imaging)
     float* se = sg + (ADJ ? TZ * kTX : 0);            // [2][TZ][kTX] eps and 1/(1+eps) (SE)
@@ -422,6 +423,18 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
     if (tid == 0) {
         for (int j = 0; j < NS; ++j) mbar_init(&bar[j], 1);
         fence_mbar_init();
+    }
+    // The tap tables are written before the call's first step and never by a
+    // step, so the group's tap ranges are read here, ahead of
+    // griddepcontrol.wait, one thread per shot.
+    if (sparse && tid < ns) {
+        const int kcell = TZ / a.TZc;
+        const int cbase = ((s0 + tid) * a.ncx + (int)blockIdx.x) * a.ncz;
+        const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
+        taprng[tid][0] = a.inj.cell_start ? a.inj.cell_start[cbase + c0] : 0;
+        taprng[tid][1] = a.inj.cell_start ? a.inj.cell_start[cbase + c1] : 0;
+        taprng[tid][2] = a.gat.cell_start ? a.gat.cell_start[cbase + c0] : 0;
+        taprng[tid][3] = a.gat.cell_start ? a.gat.cell_start[cbase + c1] : 0;
     }
     __syncthreads();
     // Programmatic dependent launch: the next step's CTAs may be scheduled once
@@ -587,17 +600,10 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
         // decisions below are uniform over the CTA).
         int ib = 0, ie = 0, gb = 0, ge = 0;
         if (sparse) {
-            const int kcell = TZ / a.TZc;
-            const int cbase = (shot * a.ncx + (int)blockIdx.x) * a.ncz;
-            const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
-            if (a.inj.cell_start) {
-                ib = a.inj.cell_start[cbase + c0];
-                ie = a.inj.cell_start[cbase + c1];
-            }
-            if (a.gat.cell_start) {
-                gb = a.gat.cell_start[cbase + c0];
-                ge = a.gat.cell_start[cbase + c1];
-            }
+            ib = taprng[i][0];
+            ie = taprng[i][1];
+            gb = taprng[i][2];
+            ge = taprng[i][3];
         }
         const bool taps = ie > ib || ge > gb;
         // the stage is refilled by shot i + NS's copies, and taps touch other threads' points
