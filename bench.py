@@ -43,18 +43,21 @@ VARIANT_KERNEL = {(0, 18): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,fwd>"),
                   (1, 16): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,0,adj>"),
                   (1, 25): ("k_step2d_sgt", "k_step2d_sgt<16,8,2,1,adj>")}
 # shot-group TMA kernels with deeper rings and the adjoint's forward level by TMA
-for _k, _fl, _g in ((39, 9, 2), (40, 9, 4), (41, 17, 4), (42, 9, 8), (43, 17, 8)):
+for _k, _fl, _g in ((39, 9, 2), (40, 9, 4), (41, 17, 4), (42, 9, 8), (43, 17, 8), (44, 41, 4), (45, 33, 2), (46, 41, 8), (47, 49, 4)):
     VARIANT_KERNEL[(0, _k)] = ("k_step2d_sgt", "k_step2d_sgt<16,8,%d,%d,fwd>" % (_g, _fl))
-for _k, _fl, _g in ((37, 5, 2), (38, 13, 2), (39, 13, 4), (40, 5, 4)):
+for _k, _fl, _g in ((37, 5, 2), (38, 13, 2), (39, 13, 4), (40, 5, 4), (41, 69, 4), (42, 101, 4), (43, 37, 4), (44, 101, 8), (45, 45, 4), (46, 101, 2)):
     VARIANT_KERNEL[(1, _k)] = ("k_step2d_sgt", "k_step2d_sgt<16,8,%d,%d,adj>" % (_g, _fl))
 # the z-window kernels (step2d_zw.cu): (TZ, BZ, G) of forward variants 33-38 and adjoint variants 31-36
 for _i, _c in enumerate([(16, 4, 2), (16, 4, 4), (16, 2, 2), (32, 8, 2), (32, 4, 2), (16, 8, 2)]):
     for _which, _base, _tag in ((0, 33, "fwd"), (1, 31, "adj")):
         VARIANT_KERNEL[(_which, _base + _i)] = ("k_step2d_zw", "k_step2d_zw<%d,%d,%d,%s>" % (*_c, _tag),
                                                 "step2d_zw.cu")
-TRAFFIC = {("k_step2d_sgt<16,8,2,1,fwd>", "2badfa07c7efa163"): 53.42e6,
-           ("k_step2d_sgt<16,8,2,1,adj>", "2badfa07c7efa163"): 95.74e6,
-           ("k_step2d_sgt<16,8,4,5,adj>", "2badfa07c7efa163"): 87.00e6,
+TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "482171260dd51c75"): 53.40e6,
+           ("k_step2d_sgt<16,8,2,1,fwd>", "482171260dd51c75"): 53.40e6,
+           ("k_step2d_sgt<16,8,4,9,fwd>", "482171260dd51c75"): 53.40e6,
+           ("k_step2d_sgt<16,8,2,0,adj>", "482171260dd51c75"): 96.02e6,
+           ("k_step2d_sgt<16,8,2,1,adj>", "482171260dd51c75"): 96.26e6,
+           ("k_step2d_sgt<16,8,4,5,adj>", "482171260dd51c75"): 87.41e6,
            ("k_step3d_tma<8,64,10,fwd>", "edf5911651f90434"): 1385.46e6}
 
 

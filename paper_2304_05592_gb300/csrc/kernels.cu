@@ -368,14 +368,17 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
 // padded grid) into a ring of NS stages (2 by default, 3 or 4 with FL bits 8
 // or 16): one thread keeps the loads of the next NS - 1 shots in flight while
 // shot i is computed.  FL bit 1 adds the previous level's tile to a stage,
-// bit 4 (adjoint) the forward level u^k.  Row offsets, the model and the sponge
+// bit 4 (adjoint) the forward level u^k; bit 32 orders the grid so that the
+// top tile rows, which hold the source and receiver taps and take longest,
+// are dispatched first; bit 64 sizes registers for 3 CTAs per SM (what the
+// shared memory of the adjoint's 2-stage u^k ring allows anyway).  Row offsets, the model and the sponge
 // factors are set up once per CTA in 32-bit form, so the per-shot work is the
 // stencil arithmetic, one load of the previous level and one store per 4
 // points.  Waits on the ring are bounded; on a timeout the CTA records
 // kErrTimeout, lets its issued copies land and returns.
 template <int TZ, int BZ, int G, int FL, bool ADJ>
 __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
-                                          : (FL & 8) ? 768 / (32 * BZ)
+                                          : ((FL & 8) || (FL & 64)) ? 768 / (32 * BZ)
                                           : (FL & 2) ? 1280 / (32 * BZ)
                                           : ((TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 512 / (32 * BZ)))
     k_step2d_sgt(const __grid_constant__ StepMaps mp, const StepArgs a)
@@ -399,8 +402,14 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
     const CUtensorMap* mh = ADJ ? &mp.halo_a : &mp.halo_f;
     const CUtensorMap* mt = ADJ ? &mp.tile_a : &mp.tile_f;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int x0 = blockIdx.x * kTX, z0 = blockIdx.y * TZ;
-    const int grp = blockIdx.z, s0 = grp * G, ns = min(G, a.nshot - s0);
+    // grid (x tiles, z tiles, groups), or with FL bit 32 (x tiles, groups, z
+    // tiles): CTAs are dispatched in linear block order, so the second form
+    // runs every group of the top tile rows (where sources and receivers sit)
+    // in the first wave
+    constexpr bool GM = (FL & 32) != 0;
+    const int tzi = GM ? (int)blockIdx.z : (int)blockIdx.y;
+    const int x0 = blockIdx.x * kTX, z0 = tzi * TZ;
+    const int grp = GM ? (int)blockIdx.y : (int)blockIdx.z, s0 = grp * G, ns = min(G, a.nshot - s0);
     const int lx = 4 * tx, gx = x0 + lx;
     const int nvalid = min(4, a.Nx - gx);
     const bool imaging = ADJ && a.gacc != nullptr;
@@ -430,7 +439,7 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
     if (sparse && tid < ns) {
         const int kcell = TZ / a.TZc;
         const int cbase = ((s0 + tid) * a.ncx + (int)blockIdx.x) * a.ncz;
-        const int c0 = (int)blockIdx.y * kcell, c1 = min(c0 + kcell, a.ncz);
+        const int c0 = tzi * kcell, c1 = min(c0 + kcell, a.ncz);
         taprng[tid][0] = a.inj.cell_start ? a.inj.cell_start[cbase + c0] : 0;
         taprng[tid][1] = a.inj.cell_start ? a.inj.cell_start[cbase + c1] : 0;
         taprng[tid][2] = a.gat.cell_start ? a.gat.cell_start[cbase + c0] : 0;
@@ -1721,7 +1730,8 @@ static const Variant2D kFwd2D[] = {{0, 32, 4, 0, 0}, {1, 48, 6, 2, 0}, {1, 32, 4
                                    {4, 16, 8, 1, 4}, {4, 8, 8, 1, 4}, {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2},
                                    {4, 16, 8, 2, 4},  {7, 16, 4, 0, 2}, {7, 16, 4, 1, 4}, {7, 16, 2, 2, 2},
                                    {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2}, {7, 16, 8, 5, 2}, {4, 16, 8, 9, 2},
-                                   {4, 16, 8, 9, 4},  {4, 16, 8, 17, 4}, {4, 16, 8, 9, 8}, {4, 16, 8, 17, 8}};
+                                   {4, 16, 8, 9, 4},  {4, 16, 8, 17, 4}, {4, 16, 8, 9, 8}, {4, 16, 8, 17, 8}, {4, 16, 8, 41, 4},
+                                   {4, 16, 8, 33, 2},  {4, 16, 8, 41, 8}, {4, 16, 8, 49, 4}};
 static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2, 4, 0}, {1, 32, 4, 2, 0},
                                    {2, 32, 8, 0, 4}, {2, 16, 8, 0, 4}, {2, 32, 8, 0, 8}, {2, 16, 8, 0, 2},
                                    {3, 24, 4, 1, 0}, {3, 24, 4, 2, 0}, {3, 48, 4, 2, 0}, {3, 16, 8, 2, 0},
@@ -1732,7 +1742,8 @@ static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2
                                    {4, 16, 8, 2, 2}, {4, 16, 8, 3, 2}, {4, 16, 8, 2, 4},  {7, 16, 4, 0, 2},
                                    {7, 16, 4, 1, 4}, {7, 16, 2, 2, 2}, {7, 32, 8, 3, 2},  {7, 32, 4, 4, 2},
                                    {7, 16, 8, 5, 2}, {4, 16, 8, 5, 2}, {4, 16, 8, 13, 2}, {4, 16, 8, 13, 4},
-                                   {4, 16, 8, 5, 4}};
+                                   {4, 16, 8, 5, 4}, {4, 16, 8, 69, 4}, {4, 16, 8, 101, 4}, {4, 16, 8, 37, 4},
+                                   {4, 16, 8, 101, 8}, {4, 16, 8, 45, 4}, {4, 16, 8, 101, 2}};
 // 3D variants (which = 2; TZ = planes per CTA, R = tile rows in y, NST = ring
 // slots, G = 1 for the ring without block barriers, G = PF + 1 for the ring
 // whose model and previous level arrive PF planes ahead by cp.async): kind 0
@@ -1742,7 +1753,7 @@ static const Variant2D k3D[] = {{0, 32, 8, 0, 0},  {6, 32, 8, 7, 0},  {6, 64, 8,
                                 {6, 64, 8, 10, 1}, {6, 64, 8, 12, 1}, {6, 96, 8, 12, 1}, {6, 64, 8, 8, 4},
                                 {6, 64, 8, 7, 5},  {6, 96, 8, 8, 4}};
 static int g_selected[3] = {-1, -1, -1};
-static const int kDefaultVariant[3] = {18, 16, 5};
+static const int kDefaultVariant[3] = {44, 42, 5};
 
 int variant_count(int which)
 {
@@ -1834,7 +1845,8 @@ static void launch_2d_group_tma(const StepArgs& a, const StepMaps* maps, cudaStr
     // launched with programmatic stream serialization: consecutive steps overlap the
     // launch and set-up of one with the last CTAs of the other (see the kernel)
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
+    cfg.gridDim = (FL & 32) ? dim3(a.ncx, (a.nshot + G - 1) / G, (a.Nz + TZ - 1) / TZ)
+                            : dim3(a.ncx, (a.Nz + TZ - 1) / TZ, (a.nshot + G - 1) / G);
     cfg.blockDim = dim3(32, BZ);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -1961,6 +1973,10 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 41: launch_2d_group_tma<16, 8, 4, false, 17>(a, maps, s); break;
             case 42: launch_2d_group_tma<16, 8, 8, false, 9>(a, maps, s); break;
             case 43: launch_2d_group_tma<16, 8, 8, false, 17>(a, maps, s); break;
+            case 44: launch_2d_group_tma<16, 8, 4, false, 9 | 32>(a, maps, s); break;
+            case 45: launch_2d_group_tma<16, 8, 2, false, 1 | 32>(a, maps, s); break;
+            case 46: launch_2d_group_tma<16, 8, 8, false, 9 | 32>(a, maps, s); break;
+            case 47: launch_2d_group_tma<16, 8, 4, false, 17 | 32>(a, maps, s); break;
             default: launch_2d_direct<32, 8, false>(a, s); break;
             }
         } else {
@@ -1999,6 +2015,12 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
             case 38: launch_2d_group_tma<16, 8, 2, true, 13>(a, maps, s); break;
             case 39: launch_2d_group_tma<16, 8, 4, true, 13>(a, maps, s); break;
             case 40: launch_2d_group_tma<16, 8, 4, true, 5>(a, maps, s); break;
+            case 41: launch_2d_group_tma<16, 8, 4, true, 5 | 64>(a, maps, s); break;
+            case 42: launch_2d_group_tma<16, 8, 4, true, 5 | 32 | 64>(a, maps, s); break;
+            case 43: launch_2d_group_tma<16, 8, 4, true, 5 | 32>(a, maps, s); break;
+            case 44: launch_2d_group_tma<16, 8, 8, true, 5 | 32 | 64>(a, maps, s); break;
+            case 45: launch_2d_group_tma<16, 8, 4, true, 13 | 32>(a, maps, s); break;
+            case 46: launch_2d_group_tma<16, 8, 2, true, 5 | 32 | 64>(a, maps, s); break;
             default: launch_2d_direct<32, 8, true>(a, s); break;
             }
         }
