@@ -52,12 +52,8 @@ for _i, _c in enumerate([(16, 4, 2), (16, 4, 4), (16, 2, 2), (32, 8, 2), (32, 4,
     for _which, _base, _tag in ((0, 33, "fwd"), (1, 31, "adj")):
         VARIANT_KERNEL[(_which, _base + _i)] = ("k_step2d_zw", "k_step2d_zw<%d,%d,%d,%s>" % (*_c, _tag),
                                                 "step2d_zw.cu")
-TRAFFIC = {("k_step2d_sgt<16,8,2,0,fwd>", "482171260dd51c75"): 53.40e6,
-           ("k_step2d_sgt<16,8,2,1,fwd>", "482171260dd51c75"): 53.40e6,
-           ("k_step2d_sgt<16,8,4,9,fwd>", "482171260dd51c75"): 53.40e6,
-           ("k_step2d_sgt<16,8,2,0,adj>", "482171260dd51c75"): 96.02e6,
-           ("k_step2d_sgt<16,8,2,1,adj>", "482171260dd51c75"): 96.26e6,
-           ("k_step2d_sgt<16,8,4,5,adj>", "482171260dd51c75"): 87.41e6,
+TRAFFIC = {("k_step2d_sgt<16,8,4,41,fwd>", "63961bb819ec2242"): 53.40e6,
+           ("k_step2d_sgt<16,8,4,101,adj>", "63961bb819ec2242"): 87.59e6,
            ("k_step3d_tma<8,64,10,fwd>", "edf5911651f90434"): 1385.46e6}
 
 
