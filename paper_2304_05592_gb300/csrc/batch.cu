@@ -709,12 +709,19 @@ bool valid_grid(const wave_grid_t& g)
 }
 
 // Tiles of every problem for tile height TZ (the flag and tile tables are
-// sized for the smallest tile height of any variant).
+// sized for the smallest tile height of any variant).  Problems take tile
+// numbers in order of decreasing nt: the tiles still stepping at any time are
+// then a prefix of the numbering, and the sweeps' round-robin assignment
+// (tile t to CTA t mod grid) keeps every CTA within one tile of the others
+// as the shorter problems finish.
 void layout_tiles(BatchLayout& B, int TZ)
 {
     B.TZ = TZ;
     B.ntile = 0;
-    for (size_t i = 0; i < B.hp.size(); ++i) {
+    std::vector<int> order(B.hp.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return B.hp[x].d.nt > B.hp[y].d.nt; });
+    for (const int i : order) {
         HostProb& h = B.hp[i];
         h.ntz = (h.d.Nz + TZ - 1) / TZ;
         h.tile0 = B.ntile;
