@@ -54,7 +54,7 @@ for _i, _c in enumerate([(16, 4, 2), (16, 4, 4), (16, 2, 2), (32, 8, 2), (32, 4,
                                                 "step2d_zw.cu")
 TRAFFIC = {("k_step2d_sgt<16,8,4,41,fwd>", "63961bb819ec2242"): 53.40e6,
            ("k_step2d_sgt<16,8,4,101,adj>", "63961bb819ec2242"): 87.59e6,
-           ("k_step3d_tma<8,64,10,fwd>", "edf5911651f90434"): 1385.46e6}
+           ("k_step3d_tma<8,76,8,fwd>", "edf5911651f90434"): 1385.73e6}
 
 
 def parse():
@@ -276,9 +276,9 @@ def cpu_baseline(nt: int):
 
 
 def _variant3d(v: int) -> str:
-    """Label of a 3D step variant; -1 is the library default, variant 5 (TMA plane
-    ring, 8-row tiles, 64 planes per CTA, 10 ring slots), whose traffic was captured."""
-    return "5 (k_step3d_tma<8,64,10>)" if v in (-1, 5) else str(v)
+    """Label of a 3D step variant; -1 is the library default, variant 16 (TMA plane
+    ring, 8-row tiles, 76 planes per CTA, 8 ring slots), whose traffic was captured."""
+    return "16 (k_step3d_tma<8,76,8>)" if v in (-1, 16) else str(v)
 
 
 def config3_forward(dev, peak, nt: int = 200, variant: int = -1):
@@ -307,8 +307,8 @@ def config3_forward(dev, peak, nt: int = 200, variant: int = -1):
                         f"{p.nt} of the 2000 steps", "pt_updates_per_s": N * (p.nt - 1) / el,
             "kernel": f"3D step variant {_variant3d(variant)}", "avg_launch_us": avg * 1e6,
             "achieved_gbs": ach, "frac": ach / peak,
-            "traffic": TRAFFIC.get(("k_step3d_tma<8,64,10,fwd>", kernel_hash("k_step3d_tma")))
-            if variant in (-1, 5) else None,
+            "traffic": TRAFFIC.get(("k_step3d_tma<8,76,8,fwd>", kernel_hash("k_step3d_tma")))
+            if variant in (-1, 16) else None,
             "bound": "hbm", "bytes_per_point": 16}
 
 

@@ -1751,9 +1751,10 @@ static const Variant2D kAdj2D[] = {{0, 32, 4, 0, 0}, {1, 24, 3, 3, 0}, {1, 16, 2
 static const Variant2D k3D[] = {{0, 32, 8, 0, 0},  {6, 32, 8, 7, 0},  {6, 64, 8, 7, 0},  {6, 32, 16, 7, 0},
                                 {6, 64, 16, 7, 0}, {6, 64, 8, 10, 0}, {6, 32, 8, 10, 0}, {6, 96, 8, 10, 0},
                                 {6, 64, 8, 10, 1}, {6, 64, 8, 12, 1}, {6, 96, 8, 12, 1}, {6, 64, 8, 8, 4},
-                                {6, 64, 8, 7, 5},  {6, 96, 8, 8, 4}};
+                                {6, 64, 8, 7, 5},  {6, 96, 8, 8, 4},  {6, 76, 8, 10, 0},
+                                {6, 76, 8, 12, 0}, {6, 76, 8, 8, 0}};
 static int g_selected[3] = {-1, -1, -1};
-static const int kDefaultVariant[3] = {44, 42, 5};
+static const int kDefaultVariant[3] = {44, 42, 16};
 
 int variant_count(int which)
 {
@@ -2039,6 +2040,9 @@ static void launch_step_raw(const Tiling& t, int ndim, bool adjoint, const StepA
         case 11: launch_3d_tma<8, 64, 8, 3>(adjoint, a, maps, s); break;
         case 12: launch_3d_tma<8, 64, 7, 4>(adjoint, a, maps, s); break;
         case 13: launch_3d_tma<8, 96, 8, 3>(adjoint, a, maps, s); break;
+        case 14: launch_3d_tma<8, 76, 10>(adjoint, a, maps, s); break;
+        case 15: launch_3d_tma<8, 76, 12>(adjoint, a, maps, s); break;
+        case 16: launch_3d_tma<8, 76, 8>(adjoint, a, maps, s); break;
         default: {
             const int ntz = (a.Nz + 31) / 32;
             dim3 grid(t.ncx, t.ncy, ntz * a.nshot);

@@ -63,7 +63,7 @@ Tiling choose_tiling(const Dims& d, int nshot)
         }
     } else {
         t.TY = 8;
-        t.TZc = 32;
+        t.TZc = 4;  // divides every 3D variant's planes per CTA (32, 64, 76, 96)
         t.v3 = current_variant(2);
     }
     t.ncx = (d.Nx + t.TX - 1) / t.TX;
