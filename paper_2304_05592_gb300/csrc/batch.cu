@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(32 * kBBZ, 2)
 // makes every other wait of the sweep give up too, and each warp leaves only
 // after the copies it issued have landed.
 struct ItemInfo {
-    int prob, tile, step, end;
+    int prob, tile, step, end, taps;  // taps: the tile has sources or receivers
 };
 
 template <int TZ, bool ADJ>
@@ -387,14 +387,20 @@ __global__ void __launch_bounds__(32 * (BZ + 2))
                 const int pi = tile_prob[t];
                 const BProb& p = probs[pi];
                 if (step >= p.nt - 1) continue;
+                const int local = t - p.tile0;
+                const int tz = local / p.ncx, tx = local - tz * p.ncx;
+                // whether the consumers have a sparse phase for the tile: looked up
+                // here, off their path (the loads overlap the waits below)
+                const TapList& inj = ADJ ? p.rec : p.src;
+                const int c0 = tz * (TZ / kTZc2), c1 = min(c0 + TZ / kTZc2, p.ncz), cb = tx * p.ncz;
+                const int taps = (inj.ntap > 0 && inj.cell_start[cb + c1] > inj.cell_start[cb + c0]) ||
+                                 (!ADJ && p.rec.ntap > 0 && p.rec.cell_start[cb + c1] > p.rec.cell_start[cb + c0]);
                 const int stage = it % NS;
                 if (it >= NS && !mbar_wait_abort(&empty[stage], (uint32_t)((it / NS) - 1) & 1u, abort_word,
                                                  kStageWaitNs)) {
                     ok = false;
                     break;
                 }
-                const int local = t - p.tile0;
-                const int tz = local / p.ncx, tx = local - tz * p.ncx;
                 bool mine = true;
                 if (lane < 9) {
                     const int nz = tz + lane / 3 - 1, nx = tx + lane % 3 - 1;
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(32 * (BZ + 2))
                 }
                 if (lane == 0) {
                     fence_proxy_async_global();  // other CTAs' plain stores before this CTA's TMA reads
-                    info[stage] = ItemInfo{pi, t, step, 0};
+                    info[stage] = ItemInfo{pi, t, step, 0, taps};
                     float* sb = st + stage * SL::floats;
                     const CUtensorMap* m = maps + (size_t)pi * kMaps;
                     const int x0 = tx * kTX, z0 = tz * TZ;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(32 * (BZ + 2))
             if (it < NS ||
                 mbar_wait_abort(&empty[stage], (uint32_t)((it / NS) - 1) & 1u, abort_word, kStageWaitNs)) {
                 if (lane == 0) {
-                    info[stage] = ItemInfo{-1, -1, -1, 1};
+                    info[stage] = ItemInfo{-1, -1, -1, 1, 0};
                     mbar_arrive(&full[stage]);
                 }
                 posted = true;
@@ -628,12 +634,7 @@ __global__ void __launch_bounds__(32 * (BZ + 2))
         }
         mbar_arrive(&empty[stage]);  // this thread is done with the stage
         // the tile's sources / receivers (block-uniform decision)
-        const TapList& inj = ADJ ? p.rec : p.src;
-        const int kcell = TZ / kTZc2;
-        const int c0 = tz * kcell, c1 = min(c0 + kcell, p.ncz), cb = tx * p.ncz;
-        const bool taps = (inj.ntap > 0 && inj.cell_start[cb + c1] > inj.cell_start[cb + c0]) ||
-                          (!ADJ && p.rec.ntap > 0 && p.rec.cell_start[cb + c1] > p.rec.cell_start[cb + c0]);
-        if (taps) {
+        if (it.taps) {
             cbar();  // the tile's points are written before taps touch them
             batch_sparse<ADJ>(p, tz, tx, TZ, n, un, ctid, NC, cbar);
         }
