@@ -351,7 +351,8 @@ constexpr int kRelSlots = 8;  // release ring between consumers and the releaser
 template <int TZ, int BZ, int NS, bool ADJ>
 __global__ void __launch_bounds__(32 * (BZ + 2))
     k_batch_sweep_tma(const BProb* __restrict__ probs, const CUtensorMap* __restrict__ maps,
-                      const int* __restrict__ tile_prob, int ntile, int nsteps, int* flags, int* err, int* abort_word)
+                      const int* __restrict__ tile_prob, const int* __restrict__ order, int ntile, int nsteps,
+                      int* flags, int* err, int* abort_word)
 {
     using SL = StageLayout<TZ, ADJ>;
     constexpr int SW = SL::SW;
@@ -383,7 +384,8 @@ __global__ void __launch_bounds__(32 * (BZ + 2))
         int it = 0;
         bool ok = true;
         for (int step = 0; step < nsteps && ok; ++step) {
-            for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            for (int q = blockIdx.x; q < ntile && ok; q += gridDim.x) {
+                const int t = order[q];  // position q of the round-robin holds tile t
                 const int pi = tile_prob[t];
                 const BProb& p = probs[pi];
                 if (step >= p.nt - 1) continue;
@@ -674,6 +676,9 @@ struct BatchLayout {
     int ntile = 0, maxnt = 0, ntile_cap = 0, TZ = 0;
     BProb* d_probs = nullptr;
     int* d_tile_prob = nullptr;
+    // per sweep (forward, adjoint): position q of the round-robin -> tile
+    std::vector<int> order[2];
+    int* d_order[2] = {nullptr, nullptr};
     CUtensorMap* d_maps = nullptr;
     std::vector<CUtensorMap> maps;
     int* flags = nullptr;
@@ -769,6 +774,8 @@ wave_status_t plan_batch(const wave_problem_t* probs, int nprob, int store, void
     Carver c(base);
     B.d_probs = c.take<BProb>(nprob);
     B.d_tile_prob = c.take<int>(B.ntile_cap);
+    B.d_order[0] = c.take<int>(B.ntile_cap);
+    B.d_order[1] = c.take<int>(B.ntile_cap);
     B.flags = c.take<int>(B.ntile_cap);
     B.d_maps = c.take<CUtensorMap>((size_t)nprob * kMaps);
     B.err = c.take<int>(4);
@@ -956,18 +963,26 @@ cudaLaunchConfig_t sweep_config(int grid, int threads, size_t smem, bool coopera
     return cfg;
 }
 
+// CTAs of a kind-1 sweep: as many as are resident at once (0: does not fit).
+template <int TZ, int BZ, int NS, bool ADJ>
+int tma_grid(const BatchLayout& B, int cap)
+{
+    const int per = tma_per_sm<TZ, BZ, NS, ADJ>();
+    if (per < 1) return 0;
+    return std::max(1, std::min(B.ntile, num_sms_batch() * (cap > 0 ? std::min(cap, per) : per)));
+}
+
 template <int TZ, int BZ, int NS, bool ADJ>
 wave_status_t launch_tma_sweep(const BatchLayout& B, int nsteps, int cap, bool cooperative, cudaStream_t s)
 {
-    const int per = tma_per_sm<TZ, BZ, NS, ADJ>();
-    if (per < 1) return WAVE_ERR_CUDA;  // does not fit on an SM
-    const int grid = std::max(1, std::min(B.ntile, num_sms_batch() * (cap > 0 ? std::min(cap, per) : per)));
+    const int grid = tma_grid<TZ, BZ, NS, ADJ>(B, cap);
+    if (grid < 1) return WAVE_ERR_CUDA;  // does not fit on an SM
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = sweep_config(grid, 32 * (BZ + 2), tma_smem<TZ, BZ, NS, ADJ>(), cooperative, s, attr);
     count_launch();
     BCK(cudaLaunchKernelEx(&cfg, k_batch_sweep_tma<TZ, BZ, NS, ADJ>, (const BProb*)B.d_probs,
-                           (const CUtensorMap*)B.d_maps, (const int*)B.d_tile_prob, B.ntile, nsteps, B.flags, B.err,
-                           B.err + 1));
+                           (const CUtensorMap*)B.d_maps, (const int*)B.d_tile_prob, (const int*)B.d_order[ADJ ? 1 : 0],
+                           B.ntile, nsteps, B.flags, B.err, B.err + 1));
     return WAVE_OK;
 }
 
@@ -1011,15 +1026,93 @@ wave_status_t launch_sweep(const BatchLayout& B, int variant, bool adj, int nste
     return WAVE_ERR_ARG;
 }
 
-// Tile tables and TMA maps for a variant's tile height (host work, then
-// stream-ordered uploads; the host vectors stay alive until the caller syncs).
-wave_status_t prepare_variant(BatchLayout& B, int variant, cudaStream_t s)
+// CTAs of a variant's sweep (0 for the direct kernel, which takes tiles in
+// numbering order).
+int sweep_grid(const BatchLayout& B, int variant, bool adj)
 {
     const BVariant v = kBatchVariants[variant];
+    if (v.kind == 0) return 0;
+#define GRID(tz, bz, ns) \
+    if (v.TZ == tz && v.BZ == bz && v.NS == ns) return adj ? tma_grid<tz, bz, ns, true>(B, v.cap) : tma_grid<tz, bz, ns, false>(B, v.cap);
+    GRID(16, 4, 2)
+    GRID(16, 4, 3)
+    GRID(32, 8, 2)
+    GRID(32, 4, 2)
+    GRID(16, 2, 3)
+    GRID(16, 8, 2)
+    GRID(16, 8, 3)
+    GRID(16, 2, 2)
+#undef GRID
+    return 0;
+}
+
+// Round-robin order of a sweep: position q goes to CTA q mod grid.  The
+// positions keep the tiles of layout_tiles' numbering (longest problems
+// first) block by block (positions b grid .. b grid + grid - 1), so each CTA
+// still holds one position per block and the active tiles stay balanced to
+// one per CTA as problems finish.  Inside a block, tiles are handed out by
+// cost: tiles touching the sponge (sponge factors computed per point) and
+// tiles with sources or receivers (a sparse phase) cost more, and the dearest
+// go to the CTAs with the least work so far.
+void build_order(const BatchLayout& B, int grid, bool adj, std::vector<int>& order)
+{
+    order.resize(B.ntile);
+    for (int q = 0; q < B.ntile; ++q) order[q] = q;
+    if (grid <= 1 || grid >= B.ntile) return;
+    // relative costs measured per item: sponge tiles 1.4-1.65 x an interior
+    // tile, tiles with taps about 2 x
+    const float wsponge = adj ? 0.4f : 0.65f, wtaps = 1.0f;
+    std::vector<float> cost(B.ntile, 1.0f);
+    for (size_t i = 0; i < B.hp.size(); ++i) {
+        const HostProb& h = B.hp[i];
+        const BProb& p = B.bp[i];
+        const HostTaps& inj = adj ? h.hr : h.hs;
+        const int kcell = B.TZ / kTZc2;
+        for (int tz = 0; tz < h.ntz; ++tz)
+            for (int tx = 0; tx < p.ncx; ++tx) {
+                const int x0 = tx * kTX, z0 = tz * B.TZ;
+                const bool interior = p.ceps == 0.0f || (x0 >= p.nb && x0 + kTX <= p.nb + p.nx && z0 >= p.nb &&
+                                                         z0 + B.TZ <= p.nb + p.nz);
+                const int c0 = tz * kcell, c1 = std::min(c0 + kcell, p.ncz), cb = tx * p.ncz;
+                const bool taps = (!inj.idx.empty() && inj.cell_start[cb + c1] > inj.cell_start[cb + c0]) ||
+                                  (!adj && !h.hr.idx.empty() && h.hr.cell_start[cb + c1] > h.hr.cell_start[cb + c0]);
+                cost[h.tile0 + tz * p.ncx + tx] = 1.0f + (interior ? 0.0f : wsponge) + (taps ? wtaps : 0.0f);
+            }
+    }
+    std::vector<double> load(grid, 0.0);
+    std::vector<int> tiles, ctas;
+    for (int b0 = 0; b0 < B.ntile; b0 += grid) {
+        const int n = std::min(grid, B.ntile - b0);
+        tiles.resize(n);
+        ctas.resize(n);
+        for (int k = 0; k < n; ++k) {
+            tiles[k] = b0 + k;
+            ctas[k] = k;  // the CTAs that have a position in this block
+        }
+        std::stable_sort(tiles.begin(), tiles.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::stable_sort(ctas.begin(), ctas.end(), [&](int a, int b) { return load[a] < load[b]; });
+        for (int k = 0; k < n; ++k) {
+            order[b0 + ctas[k]] = tiles[k];
+            load[ctas[k]] += cost[tiles[k]];
+        }
+    }
+}
+
+// Tile tables, round-robin orders of the two sweeps and TMA maps for a
+// variant's tile height (host work, then stream-ordered uploads; the host
+// vectors stay alive until the caller syncs).  vf and va share the tile height.
+wave_status_t prepare_variant(BatchLayout& B, int vf, int va, cudaStream_t s)
+{
+    const BVariant v = kBatchVariants[vf];
     layout_tiles(B, v.TZ);
     BCK(cudaMemcpyAsync(B.d_probs, B.bp.data(), B.bp.size() * sizeof(BProb), cudaMemcpyHostToDevice, s));
     if (B.ntile)
         BCK(cudaMemcpyAsync(B.d_tile_prob, B.tile_prob.data(), B.ntile * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < 2; ++k) {
+        build_order(B, sweep_grid(B, k ? va : vf, k == 1), k == 1, B.order[k]);
+        if (B.ntile)
+            BCK(cudaMemcpyAsync(B.d_order[k], B.order[k].data(), B.ntile * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     if (v.kind == 1) {
         wave_status_t st = encode_batch_maps(B, v.TZ);
         if (st) return st;
@@ -1231,7 +1324,7 @@ wave_status_t wave_gradient_batch(wave_problem_t* probs, int nprob, int store, i
     const int va = kBatchVariants[v.second].TZ == kBatchVariants[vf].TZ ? v.second : vf;
 
     if ((st = setup_batch(B, probs, nprob, s))) return st;
-    if ((st = prepare_variant(B, vf, s))) return st;
+    if ((st = prepare_variant(B, vf, va, s))) return st;
     if ((st = clear_state(B, s))) return st;
 
     if (use_graph) {
@@ -1302,7 +1395,7 @@ wave_status_t wave_autotune_batch(wave_problem_t* probs, int nprob, int store, i
     BCK(cudaEventCreate(&e2));
     float tf[kNumBatchVariants], ta[kNumBatchVariants];
     for (int v = 0; v < kNumBatchVariants && st == WAVE_OK; ++v) {
-        if ((st = prepare_variant(B, v, s))) break;
+        if ((st = prepare_variant(B, v, v, s))) break;
         if ((st = clear_state(B, s))) break;
         if (cudaMemsetAsync(B.flags, 0, B.ntile_cap * sizeof(int), s) != cudaSuccess) st = WAVE_ERR_CUDA;
         cudaEventRecord(e0, s);
