@@ -137,6 +137,20 @@ __global__ void k_wait_probe(int* flag, int want, int* abort_word, int* err)
     if (threadIdx.x == 0 && !wait_flag(flag, want, abort_word)) atomicOr(err, kErrTimeout);
 }
 
+// 1 / x for the sponge factor (x = 1 + eps >= 1): the hardware approximation
+// refined by one Newton-Raphson step for the reciprocal, r <- r + r (1 - x r)
+// (error about 2^-24 relative: within half an ulp but for values next to a
+// rounding boundary, so the rare differences from the rounded reciprocal are
+// unbiased).  The sweeps recompute the factor for every point of every
+// sponge tile at every step, where the rounded form was most of the cost of
+// such a tile; the regular steps compute it once per CTA and round it.
+__device__ __forceinline__ float rcp_sponge(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
 // Sparse part of a tile's step, run by nthr threads (index tid) after the
 // tile's points are written: injection (forward: sources with q^n; adjoint:
 // the residual at the receivers) into un, then in the forward sweep the
@@ -270,7 +284,7 @@ __global__ void __launch_bounds__(32 * kBBZ, 2)
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(bdepth(gx + e, p.nb, p.nx), dz);
                     ev[e] = kv[e] * p.ceps * (float)(dd * dd);
-                    iv[e] = __frcp_rn(1.0f + ev[e]);
+                    iv[e] = rcp_sponge(1.0f + ev[e]);
                 }
                 update4(cv, ov, lap, kv, ev, iv, zero4, out);
 #pragma unroll
@@ -585,7 +599,7 @@ __global__ void __launch_bounds__(32 * (BZ + 2))
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(dxe[e], dz);
                     ev[e] = kv[e] * p.ceps * (float)(dd * dd);
-                    iv[e] = __frcp_rn(1.0f + ev[e]);
+                    iv[e] = rcp_sponge(1.0f + ev[e]);
                 }
                 update4(cen, um, lap, kv, ev, iv, zero4, out);
             }
@@ -1059,9 +1073,9 @@ void build_order(const BatchLayout& B, int grid, bool adj, std::vector<int>& ord
     order.resize(B.ntile);
     for (int q = 0; q < B.ntile; ++q) order[q] = q;
     if (grid <= 1 || grid >= B.ntile) return;
-    // relative costs measured per item: sponge tiles 1.4-1.65 x an interior
-    // tile, tiles with taps about 2 x
-    const float wsponge = adj ? 0.4f : 0.65f, wtaps = 1.0f;
+    // relative costs measured per item: sponge tiles 1.18 (adjoint) and 1.24
+    // (forward) x an interior tile, tiles with taps about 2 x
+    const float wsponge = adj ? 0.18f : 0.24f, wtaps = 1.0f;
     std::vector<float> cost(B.ntile, 1.0f);
     for (size_t i = 0; i < B.hp.size(); ++i) {
         const HostProb& h = B.hp[i];
