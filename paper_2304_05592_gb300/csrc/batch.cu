@@ -137,20 +137,6 @@ __global__ void k_wait_probe(int* flag, int want, int* abort_word, int* err)
     if (threadIdx.x == 0 && !wait_flag(flag, want, abort_word)) atomicOr(err, kErrTimeout);
 }
 
-// 1 / x for the sponge factor (x = 1 + eps >= 1): the hardware approximation
-// refined by one Newton-Raphson step for the reciprocal, r <- r + r (1 - x r)
-// (error about 2^-24 relative: within half an ulp but for values next to a
-// rounding boundary, so the rare differences from the rounded reciprocal are
-// unbiased).  The sweeps recompute the factor for every point of every
-// sponge tile at every step, where the rounded form was most of the cost of
-// such a tile; the regular steps compute it once per CTA and round it.
-__device__ __forceinline__ float rcp_sponge(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return fmaf(r, fmaf(-x, r, 1.0f), r);
-}
-
 // Sparse part of a tile's step, run by nthr threads (index tid) after the
 // tile's points are written: injection (forward: sources with q^n; adjoint:
 // the residual at the receivers) into un, then in the forward sweep the

@@ -25,7 +25,7 @@ namespace wave {
 __device__ __forceinline__ float leap(float c, float um, float lap, float kap, float eps)
 {
     float num = fmaf(kap, lap, fmaf(eps, um, 2.0f * c - um));
-    return num * __frcp_rn(1.0f + eps);
+    return num * rcp_sponge(1.0f + eps);
 }
 
 // The same update with an extra source term subtracted before the damping
@@ -33,7 +33,7 @@ __device__ __forceinline__ float leap(float c, float um, float lap, float kap, f
 __device__ __forceinline__ float leap_src(float c, float um, float lap, float kap, float eps, float src)
 {
     float num = fmaf(kap, lap, fmaf(eps, um, 2.0f * c - um)) - src;
-    return num * __frcp_rn(1.0f + eps);
+    return num * rcp_sponge(1.0f + eps);
 }
 
 // Born secondary source of four points: dmv .* (u^{n+1} - 2 u^n + u^{n-1}),
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(32 * BZ, 1024 / (32 * BZ)) k_step2d(const Step
             const float eps = kap * a.ceps * (float)(dd * dd);
             cen[i] = w[i + 4];
             um[i] = f4(uo[rr], i);
-            out[i] = leap1(cen[i], um[i], lap[i], kap, eps, __frcp_rn(1.0f + eps), bsrc[i]);
+            out[i] = leap1(cen[i], um[i], lap[i], kap, eps, rcp_sponge(1.0f + eps), bsrc[i]);
         }
         float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (imaging) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(32 * BZ) k_step2d_sg(const StepArgs a)
         for (int e = 0; e < 4; ++e) {
             const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
             eps[rr][e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
-            inv[rr][e] = __frcp_rn(1.0f + eps[rr][e]);
+            inv[rr][e] = rcp_sponge(1.0f + eps[rr][e]);
         }
     }
     float* gq = imaging ? a.gacc + (long long)grp * a.cell : nullptr;
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
         for (int e = 0; e < 4; ++e) {
             const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
             ev[e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
-            iv[e] = __frcp_rn(1.0f + ev[e]);
+            iv[e] = rcp_sponge(1.0f + ev[e]);
         }
         if (SE) {
             // each thread reads back only its own entries: no barrier needed
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(32 * BZ, (TZ / BZ) <= 2 ? 1024 / (32 * BZ) : 5
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
                     eps[rr][e] = f4(kp[rr], e) * a.ceps * (float)(dd * dd);
-                    inv[rr][e] = __frcp_rn(1.0f + eps[rr][e]);
+                    inv[rr][e] = rcp_sponge(1.0f + eps[rr][e]);
                 }
             }
             if (imaging) {
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(32 * NW) k_step2d_zm(const StepArgs a)
                 for (int e = 0; e < 4; ++e) {
                     const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
                     ev[e] = kv[e] * a.ceps * (float)(dd * dd);
-                    iv[e] = __frcp_rn(1.0f + ev[e]);
+                    iv[e] = rcp_sponge(1.0f + ev[e]);
                 }
                 update4(cen, um, lap, kv, ev, iv, zero4, out);
             }
@@ -1118,7 +1118,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) k_step2d_tma(const __grid_co
                     const int dd = max(sponge_depth(gx + e, a.nb, a.nx), dz);
                     kv[e] = f4(kp, e);
                     ev[e] = kv[e] * a.ceps * (float)(dd * dd);
-                    iv[e] = __frcp_rn(1.0f + ev[e]);
+                    iv[e] = rcp_sponge(1.0f + ev[e]);
                     cen[e] = w[e + 4];
                     um[e] = f4(uo, e);
                 }
@@ -1237,7 +1237,7 @@ __global__ void __launch_bounds__(32 * TY) k_step3d(const StepArgs a)
                 const float eps = kap * a.ceps * (float)(dd * dd);
                 cen[i] = w[i + 4];
                 um[i] = f4(uo, i);
-                out[i] = leap1(cen[i], um[i], lap[i], kap, eps, __frcp_rn(1.0f + eps), bsrc[i]);
+                out[i] = leap1(cen[i], um[i], lap[i], kap, eps, rcp_sponge(1.0f + eps), bsrc[i]);
             }
             float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (imaging) {
@@ -1427,7 +1427,7 @@ __global__ void __launch_bounds__(32 * TY, TY <= 8 ? 2 : 1) k_step3d_tma(const _
                 const int dd = max(dxy[e], dz);
                 const float kap = f4(kp, e);
                 const float eps = kap * a.ceps * (float)(dd * dd);
-                out[e] = leap1(cen[e], um[e], lap[e], kap, eps, __frcp_rn(1.0f + eps), 0.0f);
+                out[e] = leap1(cen[e], um[e], lap[e], kap, eps, rcp_sponge(1.0f + eps), 0.0f);
             }
             float uf[4] = {0.f, 0.f, 0.f, 0.f};
             float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1614,7 +1614,7 @@ __global__ void __launch_bounds__(32 * TY, 2) k_step3d_ws(const __grid_constant_
                 const int dd = max(dxy[e], dz);
                 const float kap = f4(kp, e);
                 const float eps = kap * a.ceps * (float)(dd * dd);
-                out[e] = leap1(cen[e], um[e], lap[e], kap, eps, __frcp_rn(1.0f + eps), 0.0f);
+                out[e] = leap1(cen[e], um[e], lap[e], kap, eps, rcp_sponge(1.0f + eps), 0.0f);
             }
             float uf[4] = {0.f, 0.f, 0.f, 0.f};
             float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2133,7 +2133,7 @@ __global__ void k_tapfac(Dims d, int ntap, const int* __restrict__ idx, const fl
     if (d.ndim == 3) dd = max(dd, sponge_depth(y, d.nb, d.ny));
     const float k = kap[i];
     const float eps = k * ceps * (float)(dd * dd);
-    fac[j] = w[j] * scale * k * __frcp_rn(1.0f + eps);
+    fac[j] = w[j] * scale * k * rcp_sponge(1.0f + eps);
 }
 
 void launch_tapfac(const Dims& d, const TapList& l, const float* kap, float scale_inj, float ceps, cudaStream_t s)

@@ -61,6 +61,19 @@ __device__ __forceinline__ void lap4_3d(const float* w, ZN zn, float* lap)
     }
 }
 
+// 1 / x for the sponge factor (x = 1 + eps >= 1): the hardware approximation
+// refined by one Newton-Raphson step for the reciprocal, r <- r + r (1 - x r).
+// The result is within about 2^-24 relative of 1 / x before its rounding, so it
+// is the rounded reciprocal except next to a rounding boundary, and unbiased
+// there.  Three instructions instead of the correctly rounded sequence: the
+// 3D steps and the batch sweeps evaluate it for every point at every step.
+__device__ __forceinline__ float rcp_sponge(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
 // Leapfrog update of one point: (kap lap + eps um + 2 c - um - src) * inv,
 // inv = 1 / (1 + eps); src is the Born secondary source (zero elsewhere).
 __device__ __forceinline__ float leap1(float c, float um, float lap, float kap, float eps, float inv, float src)

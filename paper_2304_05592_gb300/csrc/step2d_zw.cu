@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(32 * BZ, 16 / BZ) k_step2d_zw(const __grid_con
                     for (int e = 0; e < 4; ++e) {
                         const int dd = max(dxe[e], dz);
                         ev[e] = kv[e] * a.ceps * (float)(dd * dd);
-                        iv[e] = __frcp_rn(1.0f + ev[e]);
+                        iv[e] = rcp_sponge(1.0f + ev[e]);
                     }
                     update4(cen, um, lap, kv, ev, iv, zero4, out);
                 } else {
