@@ -1071,88 +1071,94 @@ __host__ __device__ inline int wg_cip(int ci) { return ((ci + 1) + 3) & ~3; }
 inline long long wg_chunks(long long npix) { return (npix + kWgChunk - 1) / kWgChunk; }
 inline long long wg_blocks(int B, long long npix) { return B * wg_chunks(npix); }
 
+// Channel-major tiles of kWgTile pixels in shared memory (row stride kWgS,
+// padded so that 8 consecutive rows start in different banks): rows 0..cop-1
+// hold dU (zero past co), then cip rows of the input (row ci all ones, the
+// bias; zero past it).  Thread (task, slice) accumulates a 4 x 4 block of
+// outputs (4 o, 4 i) over the 4-pixel groups g = slice, slice + nslice, ... of
+// each tile: 8 16-byte loads per 64 FMAs.
+constexpr int kWgS = kWgTile + 4;
+__host__ __device__ inline int wg_cop(int co) { return (co + 3) & ~3; }
+
 __global__ void k_wgrad(int ci, int co, long long npix, const float* __restrict__ dU, const float* __restrict__ in,
                         float* __restrict__ partial)
 {
     extern __shared__ __align__(16) float sm[];
-    const int cip = wg_cip(ci), g4 = cip / 4;
-    float* sD = sm;                         // [kWgTile][co + 1]
-    float* sI = sm + kWgTile * (co + 1);    // [kWgTile][cip]
-    const int b = blockIdx.y;
+    const int cip = wg_cip(ci), cop = wg_cop(co), g4 = cip / 4, ntask = (cop / 4) * g4;
+    const int nslice = blockDim.x / ntask;  // divides kWgTile / 4 (host)
+    const int nrow = cop + cip;
+    float* sD = sm;              // [cop][kWgS]
+    float* sI = sm + cop * kWgS;  // [cip][kWgS]
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const int task = tid % ntask, slice = tid / ntask;
+    const int o0 = 4 * (task / g4), i0 = 4 * (task % g4);
     const long long p0 = (long long)blockIdx.x * kWgChunk, p1 = min(p0 + (long long)kWgChunk, npix);
     const float* dUb = dU + (size_t)b * co * npix;
     const float* inb = in + (size_t)b * ci * npix;
-    const int tid = threadIdx.x, ntask = co * g4;
-    // up to two (o, 4 i) tasks per thread
-    float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    // 16-byte loads when every row of 4 pixels is aligned; the loads of a tile are
-    // issued together (unrolled) and only then scattered into shared memory
     const bool vec = (npix & 3) == 0 && (reinterpret_cast<uintptr_t>(dU) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(in) & 15) == 0;
-    const int nrow = co + cip, nld = nrow * (kWgTile / 4);  // (channel row, 4-pixel group) pieces
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
     for (long long g = p0; g < p1; g += kWgTile) {
         const int n = (int)min((long long)kWgTile, p1 - g);
-        if (vec) {
-            for (int e0 = tid; e0 < nld; e0 += 4 * blockDim.x) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * blockDim.x, r = e / (kWgTile / 4), p = 4 * (e % (kWgTile / 4));
-                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (e < nld && p < n) {
-                        if (r < co) v[u] = *reinterpret_cast<const float4*>(dUb + (size_t)r * npix + g + p);
-                        else if (r - co < ci) v[u] = *reinterpret_cast<const float4*>(inb + (size_t)(r - co) * npix + g + p);
-                        else if (r - co == ci) v[u] = make_float4(1.f, 1.f, 1.f, 1.f);
-                    }
+        // (row, 4-pixel group) pieces of the tile
+        for (int e = tid; e < nrow * (kWgTile / 4); e += blockDim.x) {
+            const int r = e / (kWgTile / 4), p = 4 * (e % (kWgTile / 4));
+            const float* src = r < co ? dUb + (size_t)r * npix : (r < cop ? nullptr : (r - cop < ci ? inb + (size_t)(r - cop) * npix : nullptr));
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src) {
+                if (vec && p + 4 <= n) {
+                    v = *reinterpret_cast<const float4*>(src + g + p);
+                } else {
+                    v.x = p < n ? src[g + p] : 0.0f;
+                    v.y = p + 1 < n ? src[g + p + 1] : 0.0f;
+                    v.z = p + 2 < n ? src[g + p + 2] : 0.0f;
+                    v.w = p + 3 < n ? src[g + p + 3] : 0.0f;
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * blockDim.x, r = e / (kWgTile / 4), p = 4 * (e % (kWgTile / 4));
-                    if (e >= nld) continue;
-                    const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float x = p + j < n ? f[j] : 0.0f;  // rows end on a multiple of 4 here
-                        if (r < co) sD[(p + j) * (co + 1) + r] = x;
-                        else sI[(p + j) * cip + (r - co)] = x;
-                    }
-                }
+            } else if (r - cop == ci) {
+                v = make_float4(p < n ? 1.f : 0.f, p + 1 < n ? 1.f : 0.f, p + 2 < n ? 1.f : 0.f, p + 3 < n ? 1.f : 0.f);
             }
-        } else {
-            for (int e = tid; e < kWgTile * co; e += blockDim.x) {
-                const int oo = e / kWgTile, p = e % kWgTile;
-                sD[p * (co + 1) + oo] = p < n ? dUb[(size_t)oo * npix + g + p] : 0.0f;
-            }
-            for (int e = tid; e < kWgTile * cip; e += blockDim.x) {
-                const int ii = e / kWgTile, p = e % kWgTile;
-                sI[p * cip + ii] = p < n ? (ii < ci ? inb[(size_t)ii * npix + g + p] : (ii == ci ? 1.0f : 0.0f)) : 0.0f;
-            }
+            *reinterpret_cast<float4*>(sm + r * kWgS + p) = v;
         }
         __syncthreads();
+        if (slice < nslice) {
+            for (int q = slice; q < kWgTile / 4; q += nslice) {
+                float4 d[4], x[4];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int task = tid + q * (int)blockDim.x;
-            if (task >= ntask) continue;
-            const int o = task / g4, i4 = task - o * g4;
-#pragma unroll 8
-            for (int p = 0; p < kWgTile; ++p) {
-                const float d = sD[p * (co + 1) + o];
-                const float4 a = *reinterpret_cast<const float4*>(&sI[p * cip + 4 * i4]);
-                acc[q].x = fmaf(d, a.x, acc[q].x);
-                acc[q].y = fmaf(d, a.y, acc[q].y);
-                acc[q].z = fmaf(d, a.z, acc[q].z);
-                acc[q].w = fmaf(d, a.w, acc[q].w);
+                for (int u = 0; u < 4; ++u) d[u] = *reinterpret_cast<const float4*>(sD + (o0 + u) * kWgS + 4 * q);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[v] = *reinterpret_cast<const float4*>(sI + (i0 + v) * kWgS + 4 * q);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        acc[u][v] = fmaf(d[u].x, x[v].x, acc[u][v]);
+                        acc[u][v] = fmaf(d[u].y, x[v].y, acc[u][v]);
+                        acc[u][v] = fmaf(d[u].z, x[v].z, acc[u][v]);
+                        acc[u][v] = fmaf(d[u].w, x[v].w, acc[u][v]);
+                    }
             }
         }
         __syncthreads();
     }
-    const size_t blk = (size_t)b * gridDim.x + blockIdx.x;
+    // sum the slices in index order through shared memory, then one row per block
+    float* red = sm;  // [nslice][cop][cip]
+    if (slice < nslice) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int task = tid + q * (int)blockDim.x;
-        if (task >= ntask) continue;
-        const int o = task / g4, i4 = task - o * g4;
-        *reinterpret_cast<float4*>(&partial[(blk * co + o) * cip + 4 * i4]) = acc[q];
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4*>(red + ((size_t)slice * cop + o0 + u) * cip + i0) =
+                make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+    }
+    __syncthreads();
+    const size_t blk = (size_t)b * gridDim.x + blockIdx.x;
+    for (int e = tid; e < co * cip; e += blockDim.x) {
+        const int o = e / cip, i = e - o * cip;
+        float t = 0.0f;
+        for (int k = 0; k < nslice; ++k) t += red[((size_t)k * cop + o) * cip + i];
+        partial[(blk * co + o) * cip + i] = t;
     }
 }
 
@@ -1542,9 +1548,15 @@ wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, 
     const long long nblk = wg_blocks(B, npix);
     if (nblk > 0x7fffffffLL || B > 65535) return WAVE_ERR_ARG;
     if (nblk > 0) {
-        const int ntask = Co * (wg_cip(Ci) / 4);
-        const int threads = std::min(1024, (((ntask + 1) / 2 + 31) / 32) * 32);
-        const size_t smem = (size_t)(kWgTile * (Co + 1) + kWgTile * wg_cip(Ci)) * sizeof(float);
+        // 4 x 4 output blocks times pixel slices (a power of two dividing the
+        // tile's 16 groups of 4), about 256 threads
+        const int ntask = (wg_cop(Co) / 4) * (wg_cip(Ci) / 4);
+        int nslice = 1;
+        while (nslice < kWgTile / 4 && ntask * nslice * 2 <= 320) nslice *= 2;
+        const int threads = ntask * nslice;
+        const size_t tile = (size_t)(wg_cop(Co) + wg_cip(Ci)) * kWgS;
+        const size_t red = (size_t)nslice * wg_cop(Co) * wg_cip(Ci);
+        const size_t smem = std::max(tile, red) * sizeof(float);
         const dim3 grid((unsigned)wg_chunks(npix), B);
         k_wgrad<<<grid, threads, smem, s>>>(Ci, Co, npix, dU, in, work);
     }
