@@ -132,8 +132,10 @@ wave_status_t fno_tensor_core_status(void);
 /* Weight gradients of a pointwise layer: dM[o][i] = sum_{b,p} dU[b][o][p] in[b][i][p],
  * dbias[o] = sum_{b,p} dU[b][o][p] (npix = Nz Nx pixels per sample), both
  * overwritten.  `work` holds fno_wgrad_work_floats(B, Ci, Co, npix) floats;
- * partial sums are combined in a fixed order, so results are repeatable.
- * dbias may be NULL. */
+ * partial sums are combined in a fixed order, so results are repeatable on a
+ * given GPU (the pixel chunks are sized to the GPU's resident blocks, so the
+ * grouping of the sums, and with it the last bits, can differ between GPU
+ * models).  dbias may be NULL. */
 size_t fno_wgrad_work_floats(int B, int Ci, int Co, long long npix);
 wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, const float* in, float* dM,
                         float* dbias, float* work, void* stream);

@@ -1062,37 +1062,38 @@ __global__ void __launch_bounds__(256) k_project(int ci, int H, long long npix, 
 }
 
 // --- weight gradients ---------------------------------------------------------------
-// Block (k, b) sums pixels [k kWgChunk, (k+1) kWgChunk) of sample b into
+// Block (k, b) sums pixels [k chunk, (k+1) chunk) of sample b into
 // partial[b nchunk + k][o][0..cip) (column ci is the bias, fed by a constant
 // 1); k_wgrad_reduce adds the blocks in index order.
-constexpr int kWgTile = 64, kWgChunk = 2048;
+// The host sizes chunk (a multiple of kWgTile, at least kWgMinChunk) so that
+// the B x nchunk blocks fill the GPU in one wave.
+constexpr int kWgTile = 64, kWgMinChunk = 512;
 
 __host__ __device__ inline int wg_cip(int ci) { return ((ci + 1) + 3) & ~3; }
-inline long long wg_chunks(long long npix) { return (npix + kWgChunk - 1) / kWgChunk; }
-inline long long wg_blocks(int B, long long npix) { return B * wg_chunks(npix); }
+inline long long wg_max_blocks(int B, long long npix) { return B * ((npix + kWgMinChunk - 1) / kWgMinChunk); }
 
 // Channel-major tiles of kWgTile pixels in shared memory (row stride kWgS,
 // padded so that 8 consecutive rows start in different banks): rows 0..cop-1
 // hold dU (zero past co), then cip rows of the input (row ci all ones, the
-// bias; zero past it).  Thread (task, slice) accumulates a 4 x 4 block of
-// outputs (4 o, 4 i) over the 4-pixel groups g = slice, slice + nslice, ... of
-// each tile: 8 16-byte loads per 64 FMAs.
+// bias; zero past it).  Thread (task, slice) accumulates 4 x 4 outputs, o =
+// oq + u cop/4 and i = iq + v cip/4 (strided, so that the threads of a warp
+// read consecutive rows: no bank conflicts), over the 4-pixel groups slice,
+// slice + nslice, ... of each tile: 8 16-byte loads per 64 FMAs.
 constexpr int kWgS = kWgTile + 4;
 __host__ __device__ inline int wg_cop(int co) { return (co + 3) & ~3; }
 
-__global__ void k_wgrad(int ci, int co, long long npix, const float* __restrict__ dU, const float* __restrict__ in,
-                        float* __restrict__ partial)
+__global__ void k_wgrad(int ci, int co, long long npix, long long chunk, const float* __restrict__ dU,
+                        const float* __restrict__ in, float* __restrict__ partial)
 {
     extern __shared__ __align__(16) float sm[];
     const int cip = wg_cip(ci), cop = wg_cop(co), g4 = cip / 4, ntask = (cop / 4) * g4;
     const int nslice = blockDim.x / ntask;  // divides kWgTile / 4 (host)
     const int nrow = cop + cip;
-    float* sD = sm;              // [cop][kWgS]
-    float* sI = sm + cop * kWgS;  // [cip][kWgS]
+    // each tile buffer: [cop][kWgS] rows of dU, then [cip][kWgS] rows of the input
     const int b = blockIdx.y, tid = threadIdx.x;
     const int task = tid % ntask, slice = tid / ntask;
-    const int o0 = 4 * (task / g4), i0 = 4 * (task % g4);
-    const long long p0 = (long long)blockIdx.x * kWgChunk, p1 = min(p0 + (long long)kWgChunk, npix);
+    const int oq = task / g4, iq = task % g4, og = cop / 4;
+    const long long p0 = (long long)blockIdx.x * chunk, p1 = min(p0 + chunk, npix);
     const float* dUb = dU + (size_t)b * co * npix;
     const float* inb = in + (size_t)b * ci * npix;
     const bool vec = (npix & 3) == 0 && (reinterpret_cast<uintptr_t>(dU) & 15) == 0 &&
@@ -1102,35 +1103,52 @@ __global__ void k_wgrad(int ci, int co, long long npix, const float* __restrict_
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-    for (long long g = p0; g < p1; g += kWgTile) {
+    // Tiles are double-buffered: the copies of tile k + 1 (cp.async, or plain
+    // loads when the rows are not 16-byte aligned) are issued before the
+    // arithmetic of tile k.
+    float* buf[2] = {sm, sm + nrow * kWgS};
+    const int npiece = nrow * (kWgTile / 4);
+    auto fill = [&](float* dst, long long g) {
         const int n = (int)min((long long)kWgTile, p1 - g);
-        // (row, 4-pixel group) pieces of the tile
-        for (int e = tid; e < nrow * (kWgTile / 4); e += blockDim.x) {
+        for (int e = tid; e < npiece; e += blockDim.x) {
             const int r = e / (kWgTile / 4), p = 4 * (e % (kWgTile / 4));
-            const float* src = r < co ? dUb + (size_t)r * npix : (r < cop ? nullptr : (r - cop < ci ? inb + (size_t)(r - cop) * npix : nullptr));
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (src) {
-                if (vec && p + 4 <= n) {
-                    v = *reinterpret_cast<const float4*>(src + g + p);
-                } else {
-                    v.x = p < n ? src[g + p] : 0.0f;
-                    v.y = p + 1 < n ? src[g + p + 1] : 0.0f;
-                    v.z = p + 2 < n ? src[g + p + 2] : 0.0f;
-                    v.w = p + 3 < n ? src[g + p + 3] : 0.0f;
-                }
-            } else if (r - cop == ci) {
-                v = make_float4(p < n ? 1.f : 0.f, p + 1 < n ? 1.f : 0.f, p + 2 < n ? 1.f : 0.f, p + 3 < n ? 1.f : 0.f);
+            float* d = dst + r * kWgS + p;
+            const float* src = r < co ? dUb + (size_t)r * npix
+                                      : (r < cop ? nullptr : (r - cop < ci ? inb + (size_t)(r - cop) * npix : nullptr));
+            if (src && vec) {
+                const int bytes = 4 * max(0, min(4, n - p));
+                cp_async16(su32(d), bytes ? src + g + p : src, bytes);  // zero fill past the pixels
+            } else if (src) {
+                *reinterpret_cast<float4*>(d) =
+                    make_float4(p < n ? src[g + p] : 0.0f, p + 1 < n ? src[g + p + 1] : 0.0f,
+                                p + 2 < n ? src[g + p + 2] : 0.0f, p + 3 < n ? src[g + p + 3] : 0.0f);
+            } else {
+                const float one = r - cop == ci ? 1.0f : 0.0f;
+                *reinterpret_cast<float4*>(d) = make_float4(p < n ? one : 0.f, p + 1 < n ? one : 0.f,
+                                                            p + 2 < n ? one : 0.f, p + 3 < n ? one : 0.f);
             }
-            *reinterpret_cast<float4*>(sm + r * kWgS + p) = v;
+        }
+        cp_async_commit();
+    };
+    if (p0 < p1) fill(buf[0], p0);
+    int cur = 0;
+    for (long long g = p0; g < p1; g += kWgTile, cur ^= 1) {
+        if (g + kWgTile < p1) {
+            fill(buf[cur ^ 1], g + kWgTile);  // the buffer tile k - 1 used (barrier below)
+            cp_async_wait_prev();
+        } else {
+            cp_async_wait_all();
         }
         __syncthreads();
+        const float* tD = buf[cur];
+        const float* tI = buf[cur] + cop * kWgS;
         if (slice < nslice) {
             for (int q = slice; q < kWgTile / 4; q += nslice) {
                 float4 d[4], x[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] = *reinterpret_cast<const float4*>(sD + (o0 + u) * kWgS + 4 * q);
+                for (int u = 0; u < 4; ++u) d[u] = *reinterpret_cast<const float4*>(tD + (oq + u * og) * kWgS + 4 * q);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) x[v] = *reinterpret_cast<const float4*>(sI + (i0 + v) * kWgS + 4 * q);
+                for (int v = 0; v < 4; ++v) x[v] = *reinterpret_cast<const float4*>(tI + (iq + v * g4) * kWgS + 4 * q);
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -1149,8 +1167,8 @@ __global__ void k_wgrad(int ci, int co, long long npix, const float* __restrict_
     if (slice < nslice) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            *reinterpret_cast<float4*>(red + ((size_t)slice * cop + o0 + u) * cip + i0) =
-                make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) red[((size_t)slice * cop + oq + u * og) * cip + iq + v * g4] = acc[u][v];
     }
     __syncthreads();
     const size_t blk = (size_t)b * gridDim.x + blockIdx.x;
@@ -1165,14 +1183,20 @@ __global__ void k_wgrad(int ci, int co, long long npix, const float* __restrict_
 __global__ void k_wgrad_reduce(int ci, int co, long long nblk, const float* __restrict__ partial,
                                float* __restrict__ dM, float* __restrict__ dbias)
 {
+    // one warp per output: lane l sums blocks l, l + 32, ... in order, then a
+    // fixed shuffle tree (the same order on every run)
     const int cip = wg_cip(ci);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (t >= co * (ci + 1)) return;
     const int o = t / (ci + 1), i = t - o * (ci + 1);
     float s = 0.0f;
-    for (long long k = 0; k < nblk; ++k) s += partial[((size_t)k * co + o) * cip + i];
-    if (i < ci) dM[(size_t)o * ci + i] = s;
-    else if (dbias) dbias[o] = s;
+    for (long long k = lane; k < nblk; k += 32) s += partial[((size_t)k * co + o) * cip + i];
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) s += __shfl_down_sync(0xffffffffu, s, w);
+    if (lane == 0) {
+        if (i < ci) dM[(size_t)o * ci + i] = s;
+        else if (dbias) dbias[o] = s;
+    }
 }
 
 // --- elementwise ------------------------------------------------------------------------
@@ -1536,7 +1560,7 @@ wave_status_t fno_tensor_core_status(void)
 size_t fno_wgrad_work_floats(int B, int Ci, int Co, long long npix)
 {
     if (B < 0 || Ci < 1 || Co < 1 || npix < 0) return 0;
-    return (size_t)wg_blocks(B, npix) * Co * wg_cip(Ci);
+    return (size_t)wg_max_blocks(B, npix) * Co * wg_cip(Ci);
 }
 
 wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, const float* in, float* dM,
@@ -1545,9 +1569,9 @@ wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, 
     if (B < 0 || Ci < 1 || Ci > 64 || Co < 1 || Co > 64 || npix < 0 || !dU || !in || !dM || !work)
         return WAVE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long nblk = wg_blocks(B, npix);
-    if (nblk > 0x7fffffffLL || B > 65535) return WAVE_ERR_ARG;
-    if (nblk > 0) {
+    if (wg_max_blocks(B, npix) > 0x7fffffffLL || B > 65535) return WAVE_ERR_ARG;
+    long long nblk = 0;
+    if (npix > 0 && B > 0) {
         // 4 x 4 output blocks times pixel slices (a power of two dividing the
         // tile's 16 groups of 4), about 256 threads
         const int ntask = (wg_cop(Co) / 4) * (wg_cip(Ci) / 4);
@@ -1556,12 +1580,24 @@ wave_status_t fno_wgrad(int B, int Ci, int Co, long long npix, const float* dU, 
         const int threads = ntask * nslice;
         const size_t tile = (size_t)(wg_cop(Co) + wg_cip(Ci)) * kWgS;
         const size_t red = (size_t)nslice * wg_cop(Co) * wg_cip(Ci);
-        const size_t smem = std::max(tile, red) * sizeof(float);
-        const dim3 grid((unsigned)wg_chunks(npix), B);
-        k_wgrad<<<grid, threads, smem, s>>>(Ci, Co, npix, dU, in, work);
+        const size_t smem = std::max(2 * tile, red) * sizeof(float);
+        cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // chunks per sample so that all blocks are resident at once
+        int per = 0, dev = 0, nsm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wgrad, threads, smem);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        (void)cudaGetLastError();
+        const long long want = std::max(1LL, (long long)std::max(per, 1) * nsm / B);
+        long long chunk = (npix + want - 1) / want;
+        chunk = std::max<long long>(kWgMinChunk, (chunk + kWgTile - 1) / kWgTile * kWgTile);
+        const long long nchunk = (npix + chunk - 1) / chunk;
+        nblk = (long long)B * nchunk;
+        const dim3 grid((unsigned)nchunk, B);
+        k_wgrad<<<grid, threads, smem, s>>>(Ci, Co, npix, chunk, dU, in, work);
     }
     const int nout = Co * (Ci + 1);
-    k_wgrad_reduce<<<(nout + 255) / 256, 256, 0, s>>>(Ci, Co, nblk, work, dM, dbias);
+    k_wgrad_reduce<<<(nout + 7) / 8, 256, 0, s>>>(Ci, Co, nblk, work, dM, dbias);
     return launched();
 }
 
