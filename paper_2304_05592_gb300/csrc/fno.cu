@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fno.h"
 #include "internal.h"
@@ -359,20 +360,130 @@ __global__ void __launch_bounds__(256) k_combine(int ci, int co, int Nz, int Nx,
     }
     for (int o = 0; o < co; ++o) {
         float acc = sB[o];
-        const float* mr = sM + o * CIMAX;
+        // weights by 16-byte loads (the same address in every thread: broadcasts)
+        const float4* mr = reinterpret_cast<const float4*>(sM + o * CIMAX);
 #pragma unroll
-        for (int i = 0; i < CIMAX; ++i) acc = fmaf(mr[i], v[i], acc);
+        for (int i4 = 0; i4 < CIMAX / 4; ++i4) {
+            const float4 w = mr[i4];
+            acc = fmaf(w.x, v[4 * i4], acc);
+            acc = fmaf(w.y, v[4 * i4 + 1], acc);
+            acc = fmaf(w.z, v[4 * i4 + 2], acc);
+            acc = fmaf(w.w, v[4 * i4 + 3], acc);
+        }
         if (T) {  // uniform over the grid
-            const float* tr = sT + o * 32;
+            const float4* tr = reinterpret_cast<const float4*>(sT + o * 32);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                acc = fmaf(tr[2 * k], tc[k], acc);
-                acc = fmaf(-tr[2 * k + 1], ts[k], acc);
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const float4 t = tr[k2];
+                acc = fmaf(t.x, tc[2 * k2], acc);
+                acc = fmaf(-t.y, ts[2 * k2], acc);
+                acc = fmaf(t.z, tc[2 * k2 + 1], acc);
+                acc = fmaf(-t.w, ts[2 * k2 + 1], acc);
             }
         }
         const size_t oi = ((size_t)b * co + o) * npix + pix;
         if (pre) pre[oi] = acc;
         stf(out, oi, act == FNO_ACT_GELU ? gelu(acc) : acc);
+    }
+}
+
+// The same combine as a register-tiled product, for CO = 32 or 64 output
+// channels: out[o][p] = bias[o] + sum_k A[k][o] B[k][p] with A = [M^T; the
+// row's spectral coefficients (sine terms negated, zero past 2 mx, 32 rows)]
+// and B = [the input tile; the x inverse-transform table of the tile's
+// pixels], k ascending, so every output is the same fmaf sequence as in
+// k_combine (bitwise the same).  A block takes 128 pixels of one row; thread
+// (oq, pq) holds outputs 4 oq .. 4 oq + 3 at pixels 4 pq .. 4 pq + 3 and
+// 64 + 4 pq .. 64 + 4 pq + 3: per k one 16-byte load of A (a broadcast) and
+// two of B feed 32 FMAs.
+constexpr int kRtP = 128, kRtS = kRtP + 4;  // pixels per block, B row stride
+template <int CO, typename Tin, typename Tout>
+__global__ void __launch_bounds__(CO * 4) k_combine_rt(int ci, int Nz, int Nx, int mx, const Tin* __restrict__ in,
+                                                   const float* __restrict__ M, int mtrans,
+                                                   const float* __restrict__ bias, const float* __restrict__ T,
+                                                   const float* __restrict__ tab, int act, float* __restrict__ pre,
+                                                   Tout* __restrict__ out)
+{
+    extern __shared__ __align__(16) float sm[];
+    constexpr int NT = CO * 4;
+    const int K = ci + (T ? 32 : 0);
+    float* sA = sm;                // [K][CO]
+    float* sB = sA + K * CO;       // [K][kRtS]
+    float* sBias = sB + K * kRtS;  // [CO]
+    const int b = blockIdx.z, z = blockIdx.y, x0 = blockIdx.x * kRtP, tid = threadIdx.x;
+    const int n2 = 2 * mx;
+    const size_t npix = (size_t)Nz * Nx, row = (size_t)z * Nx;
+    for (int e = tid; e < K * CO; e += NT) {
+        const int k = e / CO, o = e - k * CO;
+        float a;
+        if (k < ci) {
+            a = mtrans ? M[(size_t)k * CO + o] : M[(size_t)o * ci + k];
+        } else {
+            const int r = k - ci;
+            a = r < n2 ? T[(((size_t)b * CO + o) * Nz + z) * n2 + r] : 0.0f;
+            if (r & 1) a = -a;
+        }
+        sA[e] = a;
+    }
+    for (int e = tid; e < ci * kRtP; e += NT) {
+        const int i = e / kRtP, p = e - i * kRtP;
+        sB[i * kRtS + p] = x0 + p < Nx ? ldf(in, ((size_t)b * ci + i) * npix + row + x0 + p) : 0.0f;
+    }
+    if (T) {
+        for (int e = tid; e < 32 * kRtP; e += NT) {
+            const int p = e >> 5, r = e & 31;
+            sB[(ci + r) * kRtS + p] = (x0 + p < Nx && r < n2) ? tab[(size_t)(x0 + p) * n2 + r] : 0.0f;
+        }
+    }
+    for (int e = tid; e < CO; e += NT) sBias[e] = bias ? bias[e] : 0.0f;
+    __syncthreads();
+    const int oq = tid / 16, pq = tid % 16;
+    float acc[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = sBias[4 * oq + u];
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const float4 a = *reinterpret_cast<const float4*>(sA + k * CO + 4 * oq);
+        const float4 b0 = *reinterpret_cast<const float4*>(sB + k * kRtS + 4 * pq);
+        const float4 b1 = *reinterpret_cast<const float4*>(sB + k * kRtS + 64 + 4 * pq);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const size_t ob = ((size_t)b * CO + 4 * oq + u) * npix + row;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = x0 + 64 * h + 4 * pq;
+            float y[4], g[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                y[j] = acc[u][4 * h + j];
+                g[j] = act == FNO_ACT_GELU ? gelu(y[j]) : y[j];
+            }
+            if (x + 3 < Nx && ((ob + x) & 3) == 0) {  // 16-byte (8-byte for BF16) stores
+                if (pre) *reinterpret_cast<float4*>(pre + ob + x) = make_float4(y[0], y[1], y[2], y[3]);
+                if constexpr (std::is_same<Tout, float>::value) {
+                    *reinterpret_cast<float4*>(out + ob + x) = make_float4(g[0], g[1], g[2], g[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) stf(out, ob + x + j, g[j]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (x + j >= Nx) continue;
+                    if (pre) pre[ob + x + j] = y[j];
+                    stf(out, ob + x + j, g[j]);
+                }
+            }
+        }
     }
 }
 
@@ -1351,6 +1462,21 @@ void combine_dispatch(int B, int ci, int co, int Nz, int Nx, int mx, const void*
         const dim3 grid((unsigned)((npix / 4 + 255) / 256), B);
         k_combine_px4<4, Tin, Tout><<<grid, 256, 0, s>>>(ci, co, npix, static_cast<const Tin*>(in), M, mt, bias, act,
                                                          pre, static_cast<Tout*>(out));
+        return;
+    }
+    if ((co == 32 || co == 64) && ci <= 64 && (!T || mx <= 16)) {
+        const int K = ci + (T ? 32 : 0);
+        const size_t smem = (size_t)(K * co + K * kRtS + co) * sizeof(float);
+        const dim3 grid((unsigned)((Nx + kRtP - 1) / kRtP), (unsigned)Nz, (unsigned)B);
+        if (co == 32) {
+            cudaFuncSetAttribute(k_combine_rt<32, Tin, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_combine_rt<32, Tin, Tout><<<grid, 128, smem, s>>>(ci, Nz, Nx, mx, static_cast<const Tin*>(in), M, mt, bias,
+                                                                 T, tab, act, pre, static_cast<Tout*>(out));
+        } else {
+            cudaFuncSetAttribute(k_combine_rt<64, Tin, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_combine_rt<64, Tin, Tout><<<grid, 256, smem, s>>>(ci, Nz, Nx, mx, static_cast<const Tin*>(in), M, mt, bias,
+                                                                 T, tab, act, pre, static_cast<Tout*>(out));
+        }
         return;
     }
     if (ci <= 4) combine_launch<4, Tin, Tout>(B, ci, co, Nz, Nx, mx, in, M, mt, bias, T, tab, act, pre, out, s);
