@@ -649,6 +649,141 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // all but the kDxtStages - 1 most recent groups complete (kDxtStages = 3)
 __device__ __forceinline__ void cp_async_wait_stages() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
+// k_combine_rt for FP32 inputs with rows of a multiple of 4 pixels, a block
+// marching over kRzRows rows of one 128-pixel column strip: the weights, the
+// strip's x inverse table and the bias are staged once, the next row's input
+// tile arrives by cp.async and its spectral coefficients through registers
+// while the current row is computed.  The same k order and fmaf sequence as
+// k_combine (bitwise the same outputs).
+constexpr int kRzRows = 8;
+template <int CO, typename Tout>
+__global__ void __launch_bounds__(CO * 4) k_combine_rz(int ci, int Nz, int Nx, int mx, const float* __restrict__ in,
+                                                   const float* __restrict__ M, int mtrans,
+                                                   const float* __restrict__ bias, const float* __restrict__ T,
+                                                   const float* __restrict__ tab, int act, float* __restrict__ pre,
+                                                   Tout* __restrict__ out)
+{
+    extern __shared__ __align__(16) float sm[];
+    constexpr int NT = CO * 4, TPT = 32 * CO / NT;  // spectral coefficients per thread and row (8)
+    const bool spec = T != nullptr;
+    float* sW = sm;                           // [ci][CO]
+    float* sT = sW + ci * CO;                 // [2][32][CO] (spec)
+    float* sX = sT + (spec ? 2 * 32 * CO : 0);  // [2][ci][kRtS]
+    float* sTab = sX + 2 * ci * kRtS;         // [32][kRtS] (spec)
+    float* sBias = sTab + (spec ? 32 * kRtS : 0);  // [CO]
+    const int b = blockIdx.z, x0 = blockIdx.x * kRtP, tid = threadIdx.x;
+    const int z0 = blockIdx.y * kRzRows, z1 = min(z0 + kRzRows, Nz);
+    const int n2 = 2 * mx;
+    const size_t npix = (size_t)Nz * Nx;
+    for (int e = tid; e < ci * CO; e += NT) {
+        const int k = e / CO, o = e - k * CO;
+        sW[e] = mtrans ? M[(size_t)k * CO + o] : M[(size_t)o * ci + k];
+    }
+    if (spec) {
+        for (int e = tid; e < 32 * kRtP; e += NT) {
+            const int r = e / kRtP, p = e - r * kRtP;
+            sTab[r * kRtS + p] = (x0 + p < Nx && r < n2) ? tab[(size_t)(x0 + p) * n2 + r] : 0.0f;
+        }
+    }
+    for (int e = tid; e < CO; e += NT) sBias[e] = bias ? bias[e] : 0.0f;
+    // row z's input tile into buffer q (16-byte copies, zero past Nx)
+    auto issue = [&](int z, int q) {
+        float* dst = sX + q * ci * kRtS;
+        for (int e = tid; e < ci * (kRtP / 4); e += NT) {
+            const int i = e / (kRtP / 4), p = 4 * (e - i * (kRtP / 4));
+            const float* src = in + ((size_t)b * ci + i) * npix + (size_t)z * Nx;
+            const int bytes = x0 + p < Nx ? 16 : 0;  // Nx is a multiple of 4
+            cp_async16(su32(dst + i * kRtS + p), bytes ? src + x0 + p : src, bytes);
+        }
+        cp_async_commit();
+    };
+    // row z's spectral coefficients (o, r) of this thread: e = tid + j NT
+    float tn[TPT];
+    auto load_t = [&](int z) {
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            const int e = tid + j * NT, o = e >> 5, r = e & 31;
+            tn[j] = r < n2 ? T[(((size_t)b * CO + o) * Nz + z) * n2 + r] : 0.0f;
+        }
+    };
+    auto store_t = [&](int q) {
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            const int e = tid + j * NT, o = e >> 5, r = e & 31;
+            sT[(q * 32 + r) * CO + o] = (r & 1) ? -tn[j] : tn[j];
+        }
+    };
+    if (z0 < z1) {
+        issue(z0, 0);
+        if (spec) {
+            load_t(z0);
+            store_t(0);
+        }
+    }
+    const int oq = tid / 16, pq = tid % 16;
+    for (int z = z0; z < z1; ++z) {
+        const int q = (z - z0) & 1;
+        const bool next = z + 1 < z1;
+        if (next) {
+            issue(z + 1, q ^ 1);  // the buffer row z - 1 used (barrier at the end of it)
+            if (spec) load_t(z + 1);
+            cp_async_wait_prev();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const float* X = sX + q * ci * kRtS;
+        const float* A2 = sT + q * 32 * CO;
+        float acc[4][8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = sBias[4 * oq + u];
+        auto step = [&](const float* Ak, const float* Bk) {
+            const float4 a = *reinterpret_cast<const float4*>(Ak + 4 * oq);
+            const float4 b0 = *reinterpret_cast<const float4*>(Bk + 4 * pq);
+            const float4 b1 = *reinterpret_cast<const float4*>(Bk + 64 + 4 * pq);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        };
+#pragma unroll 4
+        for (int k = 0; k < ci; ++k) step(sW + k * CO, X + k * kRtS);
+        if (spec) {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) step(A2 + r * CO, sTab + r * kRtS);
+        }
+        const size_t row = (size_t)z * Nx;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t ob = ((size_t)b * CO + 4 * oq + u) * npix + row;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + 64 * h + 4 * pq;
+                if (x >= Nx) continue;  // Nx is a multiple of 4: the 4 pixels are all in or all out
+                float y[4], g[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    y[j] = acc[u][4 * h + j];
+                    g[j] = act == FNO_ACT_GELU ? gelu(y[j]) : y[j];
+                }
+                if (pre) *reinterpret_cast<float4*>(pre + ob + x) = make_float4(y[0], y[1], y[2], y[3]);
+                if constexpr (std::is_same<Tout, float>::value) {
+                    *reinterpret_cast<float4*>(out + ob + x) = make_float4(g[0], g[1], g[2], g[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) stf(out, ob + x + j, g[j]);
+                }
+            }
+        }
+        if (next && spec) store_t(q ^ 1);  // read after the barrier at the top of row z + 1
+        __syncthreads();
+    }
+}
+
 // GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2 with erf from Abramowitz and
 // Stegun, Handbook of Mathematical Functions, formula 7.1.26 (after Hastings):
 // erf(a) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-a^2), t = 1 / (1 + p a),
@@ -1463,6 +1598,24 @@ void combine_dispatch(int B, int ci, int co, int Nz, int Nx, int mx, const void*
         k_combine_px4<4, Tin, Tout><<<grid, 256, 0, s>>>(ci, co, npix, static_cast<const Tin*>(in), M, mt, bias, act,
                                                          pre, static_cast<Tout*>(out));
         return;
+    }
+    if constexpr (std::is_same<Tin, float>::value) {
+        if ((co == 32 || co == 64) && ci <= 64 && (!T || mx <= 16) && (Nx & 3) == 0 && al16 &&
+            (reinterpret_cast<uintptr_t>(T) & 15) == 0) {
+            const size_t smem = (size_t)(ci * co + (T ? 2 * 32 * co : 0) + 2 * ci * kRtS + (T ? 32 * kRtS : 0) + co) *
+                                sizeof(float);
+            const dim3 grid((unsigned)((Nx + kRtP - 1) / kRtP), (unsigned)((Nz + kRzRows - 1) / kRzRows), (unsigned)B);
+            if (co == 32) {
+                cudaFuncSetAttribute(k_combine_rz<32, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_combine_rz<32, Tout><<<grid, 128, smem, s>>>(ci, Nz, Nx, mx, static_cast<const float*>(in), M, mt, bias,
+                                                               T, tab, act, pre, static_cast<Tout*>(out));
+            } else {
+                cudaFuncSetAttribute(k_combine_rz<64, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_combine_rz<64, Tout><<<grid, 256, smem, s>>>(ci, Nz, Nx, mx, static_cast<const float*>(in), M, mt, bias,
+                                                               T, tab, act, pre, static_cast<Tout*>(out));
+            }
+            return;
+        }
     }
     if ((co == 32 || co == 64) && ci <= 64 && (!T || mx <= 16)) {
         const int K = ci + (T ? 32 : 0);
