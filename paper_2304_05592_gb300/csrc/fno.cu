@@ -1454,6 +1454,16 @@ __global__ void k_gelu_bwd(long long n, const float* __restrict__ dout, const fl
         dpre[i] = dout[i] * gelu_grad(pre[i]);
 }
 
+// The same, 4 elements per thread and 16-byte accesses (n4 = n / 4, aligned arrays).
+__global__ void k_gelu_bwd4(long long n4, const float4* __restrict__ dout, const float4* __restrict__ pre,
+                            float4* __restrict__ dpre)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 d = dout[i], x = pre[i];
+        dpre[i] = make_float4(d.x * gelu_grad(x.x), d.y * gelu_grad(x.y), d.z * gelu_grad(x.z), d.w * gelu_grad(x.w));
+    }
+}
+
 constexpr int kMseBlocks = 256;
 
 __global__ void __launch_bounds__(256) k_mse(long long n, const float* __restrict__ pred,
@@ -1884,6 +1894,14 @@ wave_status_t fno_gelu_backward(long long n, const float* dout, const float* pre
 {
     if (n < 0 || !dout || !pre || !dpre) return WAVE_ERR_ARG;
     if (n == 0) return WAVE_OK;
+    if ((n & 3) == 0 && ((reinterpret_cast<uintptr_t>(dout) | reinterpret_cast<uintptr_t>(pre) |
+                          reinterpret_cast<uintptr_t>(dpre)) & 15) == 0) {
+        const long long nb = std::min<long long>((n / 4 + 255) / 256, 16384);
+        k_gelu_bwd4<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(n / 4, reinterpret_cast<const float4*>(dout),
+                                                                   reinterpret_cast<const float4*>(pre),
+                                                                   reinterpret_cast<float4*>(dpre));
+        return launched();
+    }
     const long long nb = std::min<long long>((n + 255) / 256, 4096);
     k_gelu_bwd<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(n, dout, pre, dpre);
     return launched();
