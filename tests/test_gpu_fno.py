@@ -152,6 +152,59 @@ def test_pointwise_gelu_and_weight_gradient():
     assert rel(back.cpu().numpy(), np.einsum("oi,bo...->bi...", M, ref)) < 1e-6
 
 
+@pytest.mark.parametrize("Ci,Co,Nz,Nx,spectral,bf16_in", [(32, 32, 9, 300, True, False), (32, 64, 5, 260, False, False),
+                                                          (17, 32, 6, 70, True, False), (32, 32, 6, 256, True, True),
+                                                          (64, 64, 3, 132, True, False)])
+def test_wide_channel_mix_paths(Ci, Co, Nz, Nx, spectral, bf16_in):
+    """fno_combine for 32 or 64 output channels (the register-tiled kernels: rows
+    marched with the next row's tile by cp.async when the input is FP32 with rows of
+    a multiple of 4 pixels, one row per block otherwise), ragged 128-pixel strips
+    and row groups, with and without the spectral term, against FP64."""
+    B, mx = 2, 7
+    x = RNG.standard_normal((B, Ci, Nz, Nx))
+    M, b = RNG.standard_normal((Co, Ci)), RNG.standard_normal(Co)
+    ref = ofno.pointwise(M, b, x)
+    T = tab = None
+    if spectral:
+        Tn = RNG.standard_normal((B, Co, Nz, 2 * mx))
+        tabn = RNG.standard_normal((Nx, mx, 2))
+        ref = ref + np.einsum("bozk,xk->bozx", Tn[..., 0::2], tabn[..., 0]) - np.einsum(
+            "bozk,xk->bozx", Tn[..., 1::2], tabn[..., 1])
+        T, tab = dev(Tn), dev(tabn)
+    xin = dev(x).to(torch.bfloat16) if bf16_in else dev(x)
+    if bf16_in:
+        ref = ofno.pointwise(M, b, xin.float().cpu().numpy().astype(np.float64)) + (ref - ofno.pointwise(M, b, x))
+    pre = torch.empty((B, Co, Nz, Nx), dtype=torch.float32, device="cuda")
+    fno.fno_set_tensor_cores(False)  # the CUDA-core kernels, also for BF16 inputs
+    try:
+        out = fno.fno_combine(xin, dev(M), Co, bias=dev(b), T=T, table=tab, mx=mx, act=fno.ACT_GELU, pre=pre)
+        outt = fno.fno_combine(xin, dev(np.ascontiguousarray(M.T)), Co, m_trans=True, bias=dev(b), T=T, table=tab,
+                               mx=mx)
+    finally:
+        fno.fno_set_tensor_cores(True)
+    assert rel(pre.cpu().numpy(), ref) < 1e-6
+    assert rel(out.cpu().numpy(), ofno.gelu(ref)) < 1e-6
+    assert torch.equal(outt, pre)  # the same sums in the same order
+
+
+@pytest.mark.parametrize("Ci,Co,Nz,Nx", [(32, 32, 13, 300), (32, 64, 7, 256), (64, 1, 9, 100), (3, 32, 5, 77)])
+def test_weight_gradient_shapes(Ci, Co, Nz, Nx):
+    """fno_wgrad for the network's layer shapes (and pixel counts that leave a
+    ragged last tile or are not a multiple of 4) against FP64."""
+    B = 3
+    x, dout = RNG.standard_normal((B, Ci, Nz, Nx)), RNG.standard_normal((B, Co, Nz, Nx))
+    dM = torch.empty((Co, Ci), dtype=torch.float32, device="cuda")
+    db = torch.empty(Co, dtype=torch.float32, device="cuda")
+    work = torch.empty(fno.fno_wgrad_work_floats(B, Ci, Co, Nz * Nx), dtype=torch.float32, device="cuda")
+    fno.fno_wgrad(dev(dout), dev(x), dM, db, work)
+    gM, gb = ofno._wgrad(dout, x)
+    assert rel(dM.cpu().numpy(), gM) < 1e-5 and rel(db.cpu().numpy(), gb) < 1e-5
+    dM2 = torch.empty_like(dM)
+    db2 = torch.empty_like(db)
+    fno.fno_wgrad(dev(dout), dev(x), dM2, db2, work)
+    assert torch.equal(dM, dM2) and torch.equal(db, db2)
+
+
 def _net(cfg, Nz, Nx, B, seed):
     p = ofno.init_params(ofno.Config(**cfg.__dict__), seed)
     net = fno.FNO2d(cfg, Nz, Nx, seed=seed)
