@@ -140,6 +140,28 @@ def test_autotuned_batch_matches_oracle_bf16(wide_batch, restore_batch_variant):
     assert max(errs) < 1e-2
 
 
+def test_more_tiles_than_ctas_matches_single_shot_calls(restore_batch_variant):
+    """A batch with several tiles per CTA (sweep variant 10: one CTA per SM), so
+    that the host's cost-balanced round-robin order is in play: misfits and
+    gradients equal one wave_gradient call per problem."""
+    probs_s = synth.uneven_batch(seed=13, nshot=12, scale=0.45)
+    probs = []
+    for p in probs_s:
+        q = torch.from_numpy(oracle.ricker(p.f0, p.dt, p.nt).astype(np.float32)[:, None]).cuda()
+        v = torch.from_numpy(p.vel).cuda()
+        dob = wave.wave_forward(Grid.of(p), v, p.src, q[None].contiguous(), p.rec)[0].contiguous()
+        probs.append(BatchProblem(Grid.of(p), (v * 1.03).contiguous(), p.src[0], q, p.rec[0], dob))
+    ntile = sum(-(-(p.nx + 2 * p.nb) // 128) * -(-(p.nz + 2 * p.nb) // 16) for p in probs_s)
+    assert ntile > torch.cuda.get_device_properties(0).multi_processor_count  # several tiles per CTA
+    wave.wave_set_batch_variant(10, 10)
+    misfits, grads = wave.wave_gradient_batch(probs, store=wave.STORE_FP32, use_graph=False)
+    for p, bp, phi, gr in zip(probs_s, probs, misfits, grads):
+        phi1, g1, _ = wave.wave_gradient(Grid.of(p), bp.vel, p.src, bp.wavelet[None].contiguous(), p.rec,
+                                         bp.d_obs[None].contiguous(), store=wave.STORE_FP32)
+        assert abs(phi - phi1) <= 1e-6 * phi1
+        assert float((gr - g1).norm() / g1.norm()) < 1e-5
+
+
 def test_forced_variant_pair_must_share_tile_height(restore_batch_variant):
     with pytest.raises(wave.WaveError):
         wave.wave_set_batch_variant(0, 1)  # 32-row against 16-row tiles
