@@ -68,59 +68,84 @@ __global__ void k_tables(int Nz, int Nx, int mz, int mx, float* tf, float* ti, f
 }
 
 // --- along x: out[r][n] = sum_x in[r][x] tab[x][n], n < 2 mx ------------------
-// CTA = 256 threads, 256 rows; thread (tr, tn) owns rows 8 tr .. 8 tr + 7 and
-// outputs 4 tn .. 4 tn + 3, accumulated over x in chunks of 32 staged in
-// shared memory (rows padded to 33 floats: conflict-free in both directions).
-constexpr int kDxRows = 256, kDxChunk = 32;
+// CTA = 256 threads, kDxRows rows; thread (tr, tn) owns rows kDxRq tr ..
+// kDxRq tr + kDxRq - 1 and outputs 4 tn .. 4 tn + 3, accumulated over x in
+// chunks of 32 staged in shared memory (rows padded to 33 floats: conflict-free
+// in both directions).  The chunks are double-buffered: chunk c + 1 is loaded
+// into registers while chunk c is summed, then stored to the other buffer, one
+// block barrier per chunk.  128 rows per CTA put a 65536-row transform on the
+// GPU in one wave.
+constexpr int kDxRows = 128, kDxChunk = 32, kDxRq = kDxRows / 32;
+constexpr int kDxPv = kDxRows * kDxChunk / 256, kDxPt = kDxChunk * 32 / 256;  // elements per thread and chunk
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_dft_x(long long rows, int Nx, int n2, const T* __restrict__ in,
+__global__ void __launch_bounds__(256, 4) k_dft_x(long long rows, int Nx, int n2, const T* __restrict__ in,
                                                const float* __restrict__ tab, float* __restrict__ out)
 {
-    __shared__ float sv[kDxRows][kDxChunk + 1];
-    __shared__ __align__(16) float st[kDxChunk][32];
+    __shared__ float sv[2][kDxRows][kDxChunk + 1];
+    __shared__ __align__(16) float st[2][kDxChunk][32];
     const int tid = threadIdx.x, tn = tid & 7, tr = tid >> 3;
     const long long r0 = (long long)blockIdx.x * kDxRows;
-    float acc[8][4];
+    float acc[kDxRq][4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < kDxRq; ++q)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[q][c] = 0.0f;
-    for (int xc = 0; xc < Nx; xc += kDxChunk) {
-        // unrolled so that eight loads per thread are in flight before their stores
-#pragma unroll 8
-        for (int k = 0; k < kDxRows * kDxChunk / 256; ++k) {
+    float pv[kDxPv], pt[kDxPt];
+    auto load = [&](int xc) {
+#pragma unroll
+        for (int k = 0; k < kDxPv; ++k) {
             const int e = tid + 256 * k, row = e / kDxChunk, x = e - row * kDxChunk;
             const long long gr = r0 + row;
-            sv[row][x] = (gr < rows && xc + x < Nx) ? ldf(in, (size_t)gr * Nx + xc + x) : 0.0f;
+            pv[k] = (gr < rows && xc + x < Nx) ? ldf(in, (size_t)gr * Nx + xc + x) : 0.0f;
         }
 #pragma unroll
-        for (int k = 0; k < kDxChunk * 32 / 256; ++k) {
+        for (int k = 0; k < kDxPt; ++k) {
             const int e = tid + 256 * k, x = e >> 5, n = e & 31;
-            st[x][n] = (xc + x < Nx && n < n2) ? tab[(size_t)(xc + x) * n2 + n] : 0.0f;
+            pt[k] = (xc + x < Nx && n < n2) ? tab[(size_t)(xc + x) * n2 + n] : 0.0f;
         }
-        __syncthreads();
+    };
+    auto store = [&](int q) {
+#pragma unroll
+        for (int k = 0; k < kDxPv; ++k) {
+            const int e = tid + 256 * k, row = e / kDxChunk, x = e - row * kDxChunk;
+            sv[q][row][x] = pv[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kDxPt; ++k) {
+            const int e = tid + 256 * k;
+            st[q][e >> 5][e & 31] = pt[k];
+        }
+    };
+    load(0);
+    store(0);
+    __syncthreads();
+    int q = 0;
+    for (int xc = 0; xc < Nx; xc += kDxChunk, q ^= 1) {
+        const bool more = xc + kDxChunk < Nx;
+        if (more) load(xc + kDxChunk);  // in flight during the sums below
 #pragma unroll 4
         for (int x = 0; x < kDxChunk; ++x) {
-            const float4 t = *reinterpret_cast<const float4*>(&st[x][4 * tn]);
+            const float4 t = *reinterpret_cast<const float4*>(&st[q][x][4 * tn]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float a = sv[8 * tr + q][x];
-                acc[q][0] = fmaf(a, t.x, acc[q][0]);
-                acc[q][1] = fmaf(a, t.y, acc[q][1]);
-                acc[q][2] = fmaf(a, t.z, acc[q][2]);
-                acc[q][3] = fmaf(a, t.w, acc[q][3]);
+            for (int r = 0; r < kDxRq; ++r) {
+                const float a = sv[q][kDxRq * tr + r][x];
+                acc[r][0] = fmaf(a, t.x, acc[r][0]);
+                acc[r][1] = fmaf(a, t.y, acc[r][1]);
+                acc[r][2] = fmaf(a, t.z, acc[r][2]);
+                acc[r][3] = fmaf(a, t.w, acc[r][3]);
             }
         }
+        if (more) store(q ^ 1);  // the buffer chunk c - 1 used: free since the last barrier
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const long long gr = r0 + 8 * tr + q;
+    for (int r = 0; r < kDxRq; ++r) {
+        const long long gr = r0 + kDxRq * tr + r;
         if (gr >= rows) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (4 * tn + c < n2) out[(size_t)gr * n2 + 4 * tn + c] = acc[q][c];
+            if (4 * tn + c < n2) out[(size_t)gr * n2 + 4 * tn + c] = acc[r][c];
     }
 }
 
