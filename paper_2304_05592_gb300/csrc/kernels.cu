@@ -500,6 +500,15 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
         }
     }
 
+    // the stencil's imaging terms of this thread's points, summed over the
+    // group's shots in registers; the taps' terms (other threads' points) go to
+    // the shared tile sg, added at the end
+    float gr[RB][4];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) gr[rr][e] = 0.0f;
+
     // A thread whose wait for a stage gives up records the timeout and does no
     // further work, but passes every block barrier below (they are uniform), so
     // the CTA never splits; thread 0, which issues the copies, first waits
@@ -600,9 +609,8 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
                     uf[2] = v.z;
                     uf[3] = v.w;
                 }
-                float* g = sg + r * kTX + lx;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) g[e] -= uf[e] * (out[e] - 2.0f * cen[e] + um[e]);
+                for (int e = 0; e < 4; ++e) gr[rr][e] -= uf[e] * (out[e] - 2.0f * cen[e] + um[e]);
             }
         }
         // This CTA's taps for the shot (the same values in every thread, so the
@@ -618,8 +626,8 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
         // the stage is refilled by shot i + NS's copies, and taps touch other threads' points
         if (taps || i + NS < ns) __syncthreads();
         if (taps) {
+            // (its terms go to sg, which the stencil no longer touches before the end)
             sparse_phase<ADJ>(a, ib, ie, gb, ge, (long long)so, tid, 32 * BZ, imaging ? sg : nullptr, z0, x0);
-            if (imaging) __syncthreads();  // injection terms land in the gradient tile before the next shot
         }
     }
     if (imaging) {
@@ -627,8 +635,11 @@ __global__ void __launch_bounds__(32 * BZ, (FL & 16) ? 512 / (32 * BZ)
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr) {
             const int r = ty + rr * BZ;
-            if (live[rr])
-                *reinterpret_cast<float4*>(gq + off[rr]) = *reinterpret_cast<const float4*>(sg + r * kTX + lx);
+            if (live[rr]) {
+                const float4 t = *reinterpret_cast<const float4*>(sg + r * kTX + lx);
+                *reinterpret_cast<float4*>(gq + off[rr]) =
+                    make_float4(t.x + gr[rr][0], t.y + gr[rr][1], t.z + gr[rr][2], t.w + gr[rr][3]);
+            }
         }
     }
 }
