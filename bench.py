@@ -52,8 +52,8 @@ for _i, _c in enumerate([(16, 4, 2), (16, 4, 4), (16, 2, 2), (32, 8, 2), (32, 4,
     for _which, _base, _tag in ((0, 33, "fwd"), (1, 31, "adj")):
         VARIANT_KERNEL[(_which, _base + _i)] = ("k_step2d_zw", "k_step2d_zw<%d,%d,%d,%s>" % (*_c, _tag),
                                                 "step2d_zw.cu")
-TRAFFIC = {("k_step2d_sgt<16,8,4,41,fwd>", "a325c3c676e72a0b"): 53.39e6,
-           ("k_step2d_sgt<16,8,4,101,adj>", "a325c3c676e72a0b"): 87.60e6,
+TRAFFIC = {("k_step2d_sgt<16,8,4,41,fwd>", "2663cea1310bc711"): 53.40e6,
+           ("k_step2d_sgt<16,8,4,101,adj>", "2663cea1310bc711"): 87.59e6,
            ("k_step3d_tma<8,76,8,fwd>", "773f3f582c635e7a"): 1386.69e6}
 
 
