@@ -142,14 +142,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, uin
         : "memory");
 }
 
-// Prefetches a tile of a 4D tensor map into L2 (no shared-memory destination).
-__device__ __forceinline__ void tma_prefetch_l2_4d(const CUtensorMap* m, int c0, int c1, int c2, int c3)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
-                 ::"l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-                 : "memory");
-}
-
 // Orders global-memory accesses of the generic proxy (plain loads and stores,
 // also those of other CTAs that this thread has synchronised with) before
 // later TMA accesses of this thread.
